@@ -1,0 +1,231 @@
+/*
+ * visfly_b300.h -- C ABI of the B300 (sm_103a) rollout-step library.
+ *
+ * The library advances N quadrotors one control step and renders each agent's
+ * depth and colour image of a triangle-mesh scene, following the environment
+ * step of VisFly (arXiv 2407.14783): the user calls step(action) and receives
+ * observations (Sec. III-C).  Physics follows Sec. III-A (Eq. 1-4, body-rate
+ * controller, RK4); the depth and colour sensors follow Sec. III-B.  Reward,
+ * termination and task logic stay in the caller (Sec. III-C, Listing 1).
+ *
+ * Conventions shared by every call
+ *   - All calls return an int status (sim_status).  Nothing throws across the
+ *     ABI.  Argument, budget and CUDA launch errors are reported synchronously
+ *     and the message is available from sim_last_error() on the same thread.
+ *   - "dev" pointers are CUDA device (or managed) pointers owned by the caller;
+ *     "host" pointers are host memory owned by the caller (pinned memory makes
+ *     the copies asynchronous).  The library never frees caller memory.
+ *   - Work is enqueued on the caller's stream (cudaStream_t passed as void*,
+ *     NULL = the legacy default stream) and is asynchronous unless stated.
+ *   - Agent state is structure-of-arrays float32 [17][n]: rows 0-2 position x_W
+ *     (m, world frame, z up), 3-5 velocity v_W (m/s), 6-9 attitude quaternion
+ *     q = (w, x, y, z) body->world, 10-12 body rates Omega_B (rad/s), 13-16
+ *     rotor speeds omega_1..4 (rad/s).  Row r of agent a is at state[r*n + a].
+ *   - Commands are float32 [4][n]: normalised collective thrust u0 in [-1, 1]
+ *     and body-rate commands u1..u3 in [-1, 1] (CTBR, Sec. III-A / Sec. IV).
+ *   - Images are row-major per agent: depth float32 [n][H][W] (metres along the
+ *     optical axis, max_depth on a miss), rgb uint8 [n][H][W][3], hit id int32
+ *     [n][H][W] (original triangle index, -1 on a miss).
+ *   - Device-side faults that kernels detect (traversal stack overflow, an
+ *     iteration cap) set a device error word; sim_get_status() reports and
+ *     clears it.  Kernels never trap.
+ */
+#ifndef VISFLY_B300_H
+#define VISFLY_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sim_ctx sim_ctx;
+
+typedef enum {
+    SIM_OK = 0,
+    SIM_ERR_INVALID_ARG = -1, /* bad pointer, size, id or parameter */
+    SIM_ERR_OOM = -2,         /* device allocation failed */
+    SIM_ERR_CUDA = -3,        /* a CUDA call failed; message has the CUDA error */
+    SIM_ERR_NOT_FOUND = -4,   /* unknown scene id */
+    SIM_ERR_TRAVERSAL = -5,   /* device: BVH traversal stack overflow or iteration cap */
+    SIM_ERR_TIMEOUT = -6,     /* a bounded wait ran out */
+    SIM_ERR_BUDGET = -7       /* the context's memory budget would be exceeded */
+} sim_status;
+
+/* Model, integrator and camera parameters.  The paper names the model terms
+ * but prints no constants; every value is supplied by the caller.
+ * Rotor i sits at azimuth 45 + 90 i degrees at distance `arm` in the body x-y
+ * plane and spins in direction +1, -1, +1, -1 (X layout). */
+typedef struct sim_params {
+    float mass;          /* kg */
+    float J[3];          /* diagonal inertia, kg m^2 (Eq. 1) */
+    float arm;           /* m */
+    float k[3];          /* thrust polynomial f = k2 w^2 + k1 w + k0 (Eq. 4) */
+    float c_lag;         /* rotor time-decay constant c, 1/s (Eq. 4) */
+    float kappa;         /* rotor reaction torque / thrust, m (Eq. 3) */
+    float rho;           /* air density (Eq. 2) */
+    float Cd[3];         /* drag coefficients (Eq. 2) */
+    float area[3];       /* crossing areas (Eq. 2) */
+    float omega_min, omega_max; /* rotor speed range, rad/s */
+    float a_max;         /* mass-normalised thrust at u0 = +1, m/s^2 */
+    float rate_max[3];   /* body-rate command scale, rad/s */
+    float K_rate[3];     /* body-rate loop gains, 1/s */
+    float g;             /* gravity, m/s^2 */
+    float dt;            /* control step, s */
+    int32_t n_sub;       /* physics sub-steps per control step, 1..8 */
+    int32_t integrator;  /* 0 = RK4, 1 = explicit Euler */
+    int32_t width, height; /* image size, pixels (1..1024) */
+    float fov_deg;       /* horizontal field of view; square pixels */
+    float max_depth;     /* m; farther hits are misses */
+    float cam_off[3];    /* camera origin in the body frame, m */
+} sim_params;
+
+/* Create a context on CUDA device `device`.  The context owns scenes, BVHs, the
+ * scene table, staging buffers and the device error word; all of them count
+ * against mem_budget_bytes (0 = no limit).  *out is NULL on failure. */
+int sim_create_ctx(sim_ctx** out, int device, const sim_params* p, size_t mem_budget_bytes);
+
+/* Synchronise the device and free everything the context owns. */
+int sim_destroy_ctx(sim_ctx* ctx);
+
+/* Replace the context's parameters (affects calls enqueued afterwards). */
+int sim_set_params(sim_ctx* ctx, const sim_params* p);
+
+/* Upload a mesh and build its device BVH (Sec. III-B scenes; the BVH is an
+ * LBVH: 30-bit Morton codes of triangle centroids, radix sort, binary radix
+ * tree by longest common prefix, bottom-up AABB refit).
+ *   verts host float32 [n_verts][3]; tris host int32 [n_tris][3] (vertex
+ *   indices, validated); rgb host uint8 [n_tris][3] (flat colour per triangle).
+ * On success *scene_id_out receives the id used by sim_render.  The host
+ * arrays may be freed when the call returns (it synchronises `stream`).
+ * Errors: INVALID_ARG (bad sizes or index out of range), BUDGET, OOM, CUDA. */
+int sim_create_scene(sim_ctx* ctx, const float* verts, int64_t n_verts, const int32_t* tris, int64_t n_tris,
+                     const uint8_t* rgb, int32_t* scene_id_out, void* stream);
+
+/* Free a scene's device memory (after synchronising the device).  The id may
+ * be reused by a later sim_create_scene. */
+int sim_destroy_scene(sim_ctx* ctx, int32_t scene_id);
+
+/* Scene statistics: triangles, BVH nodes, triangles kept outside the BVH
+ * (large ones, tested by every ray), BVH depth, resident bytes. */
+typedef struct sim_scene_info {
+    int64_t n_tris, n_nodes, n_large;
+    int32_t depth, leaf_max;
+    int64_t bytes;
+} sim_scene_info;
+int sim_scene_info_get(const sim_ctx* ctx, int32_t scene_id, sim_scene_info* info);
+
+/* One control step of n agents (Sec. III-A): for each of n_sub sub-steps,
+ * body-rate controller -> rotor lag (Eq. 4) -> thrust and moment (Eq. 3) ->
+ * RK4 or Euler on Eq. 1 with drag (Eq. 2) -> quaternion normalisation.
+ *   state dev float32 [17][n], updated in place; cmd dev float32 [4][n];
+ *   ckpt dev float32 [17][n] or NULL: receives the pre-step state. */
+int sim_step(sim_ctx* ctx, int32_t n_agents, float* state, const float* cmd, float* ckpt, void* stream);
+
+/* Render every agent's depth / colour / hit-id image (Sec. III-B sensors):
+ * one primary ray per pixel centre from the camera at body offset cam_off
+ * looking along body +x (image right = body -y, image down = body -z); the
+ * closest Moller-Trumbore hit with max_depth >= t > 1e-6, equal t broken by the
+ * lowest triangle id; colour is the hit triangle's flat colour, (0,0,0) on a
+ * miss.  scene_of_agent dev int32 [n]: the scene id of each agent (ids are
+ * checked on the device; an unknown id sets SIM_ERR_NOT_FOUND in the error word
+ * and renders that agent as all misses).  Scenes of uneven size are rendered
+ * in the same launch through the context's scene table.
+ *   state dev [17][n]; depth dev float32 [n][H][W] or NULL; rgb dev uint8
+ *   [n][H][W][3] or NULL; hit_id dev int32 [n][H][W] or NULL. */
+int sim_render(sim_ctx* ctx, int32_t n_agents, const int32_t* scene_of_agent, const float* state, float* depth,
+               uint8_t* rgb, int32_t* hit_id, void* stream);
+
+/* As sim_render with every agent in one scene. */
+int sim_render_scene(sim_ctx* ctx, int32_t n_agents, int32_t scene_id, const float* state, float* depth,
+                     uint8_t* rgb, int32_t* hit_id, void* stream);
+
+/* Reverse-mode derivative of one sim_step (the dynamics are differentiable,
+ * Sec. III-A): given the pre-step state, the command and the cotangent of the
+ * post-step state, write the cotangents of the pre-step state and the command.
+ * Clamps in the controller pass the gradient inside their range (boundary
+ * included) and block it outside.  All dev float32: state_in [17][n], cmd
+ * [4][n], g_state_out [17][n] (read), g_state_in [17][n] and g_cmd [4][n]
+ * (written; they may not alias the inputs). */
+int sim_step_backward(sim_ctx* ctx, int32_t n_agents, const float* state_in, const float* cmd,
+                      const float* g_state_out, float* g_state_in, float* g_cmd, void* stream);
+
+/* T steps in one launch (one thread per agent walks the whole horizon).
+ *   state0 dev [17][n]; cmds dev [T][4][n]; states_out dev [T+1][17][n] or NULL
+ *   (all states, states_out[0] = state0); ckpt dev [ceil(T/K)][17][n] or NULL
+ *   (state at steps 0, K, 2K, ...); state_final dev [17][n] or NULL. */
+int sim_rollout(sim_ctx* ctx, int32_t n_agents, int32_t T, int32_t K, const float* state0, const float* cmds,
+                float* states_out, float* ckpt, float* state_final, void* stream);
+
+/* Reverse sweep over a rollout with recompute from checkpoints every K steps:
+ * each agent's thread re-runs K steps from a checkpoint, keeps them locally,
+ * and walks them backwards.  g_states dev [T+1][17][n] is the cotangent of
+ * every state of the trajectory (e.g. dLoss/dstate_t); outputs g_state0 dev
+ * [17][n] and g_cmds dev [T][4][n].  K must be 1..32. */
+int sim_rollout_backward(sim_ctx* ctx, int32_t n_agents, int32_t T, int32_t K, const float* ckpt,
+                         const float* cmds, const float* g_states, float* g_state0, float* g_cmds, void* stream);
+
+/* The environment step as a user calls it, with host buffers: copy the
+ * commands in, step, render, copy the images (and optionally the state) out.
+ *   cmd_host float32 [4][n]; depth_host float32 [n][H][W] or NULL; rgb_host
+ *   uint8 [n][H][W][3] or NULL; state_host float32 [17][n] or NULL (post-step
+ *   state).  The device state (state dev [17][n]) stays resident and is
+ *   updated in place.  Asynchronous on `stream`; host buffers must stay valid
+ *   until the stream reaches this point (pinned host memory for overlap). */
+int sim_env_step(sim_ctx* ctx, int32_t n_agents, const int32_t* scene_of_agent, float* state,
+                 const float* cmd_host, float* depth_host, uint8_t* rgb_host, float* state_host, void* stream);
+
+/* Ray-cast kernel configuration (the autotuner's search space).
+ *   tile_w x tile_h pixels per warp work item, rays_per_lane in {1, 2}
+ *   (tile_w * tile_h = 32 * rays_per_lane), stack_in_smem (1: per-warp stack in
+ *   shared memory, 0: stack distributed over the warp's registers), stack_depth
+ *   in {32, 64}, warps_per_cta in {2, 4, 8}, ctas_per_sm (persistent grid =
+ *   ctas_per_sm * SM count; 0 = occupancy limit). */
+typedef struct sim_render_config {
+    int32_t tile_w, tile_h, rays_per_lane, stack_in_smem, stack_depth, warps_per_cta, ctas_per_sm;
+} sim_render_config;
+int sim_get_render_config(const sim_ctx* ctx, sim_render_config* cfg);
+int sim_set_render_config(sim_ctx* ctx, const sim_render_config* cfg);
+
+/* Time every supported configuration on the given workload (each `iters`
+ * launches, CUDA events on `stream`), select the fastest and return it in
+ * *best.  times_ms (may be NULL) receives up to max_times per-config averages
+ * in the order of sim_render_config_list.  Synchronises `stream`. */
+int sim_autotune_render(sim_ctx* ctx, int32_t n_agents, const int32_t* scene_of_agent, const float* state,
+                        float* depth, uint8_t* rgb, int32_t iters, sim_render_config* best, float* times_ms,
+                        int32_t max_times, void* stream);
+/* The supported configurations (returns how many; fills up to max of them). */
+int sim_render_config_list(sim_render_config* out, int32_t max);
+
+/* Traversal counters of the last sim_render_counted call: BVH node visits and
+ * triangle tests per warp work item summed over all items, and work items. */
+typedef struct sim_render_counters {
+    int64_t node_visits, tri_tests, large_tests, items, rays;
+} sim_render_counters;
+int sim_render_counted(sim_ctx* ctx, int32_t n_agents, const int32_t* scene_of_agent, const float* state,
+                       float* depth, uint8_t* rgb, int32_t* hit_id, sim_render_counters* counters, void* stream);
+
+/* Wait for `stream` (polling, at most timeout_ms; <0 = unbounded), then read
+ * and clear the device error word.  Returns SIM_OK, SIM_ERR_TIMEOUT (work still
+ * running), SIM_ERR_CUDA, or the device-reported error. */
+int sim_get_status(sim_ctx* ctx, void* stream, int32_t timeout_ms);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* sim_last_error(const sim_ctx* ctx);
+
+/* Bytes currently allocated by the context, and its budget. */
+int sim_mem_usage(const sim_ctx* ctx, size_t* used, size_t* budget);
+
+/* Read-bandwidth probe: stream a device buffer of `bytes` (resident in L2 when
+ * it fits) `iters` times with float4 loads and report GB/s.  Synchronises. */
+int sim_probe_read_bandwidth(sim_ctx* ctx, size_t bytes, int32_t iters, double* gbs, void* stream);
+
+/* Library version string. */
+const char* sim_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VISFLY_B300_H */

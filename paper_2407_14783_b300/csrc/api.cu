@@ -1,0 +1,806 @@
+// C ABI of the rollout-step library: contexts, budgeted device memory, the
+// segmented scene table, argument checking and kernel launches.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "launch.h"
+#include "visfly_b300.h"
+
+using namespace vf;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? SIM_ERR_OOM : SIM_ERR_CUDA;
+}
+
+constexpr int kRing = 64;  // work-counter slots, so renders on different streams do not share one
+
+struct SceneRec {
+    bool live = false;
+    void* mem[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t bytes = 0;
+    int64_t n_tris = 0;
+    LbvhResult r{};
+};
+
+}  // namespace
+
+struct sim_ctx {
+    int device = 0;
+    int num_sms = 0;
+    sim_params params{};
+    DynConsts dyn{};
+    CamConsts cam{};
+    size_t budget = 0;
+    size_t used = 0;
+    std::mutex mu;
+    std::vector<SceneRec> scenes;
+    SceneRow* d_table = nullptr;
+    int table_cap = 0;
+    int* d_err = nullptr;
+    unsigned* d_ring = nullptr;  // [kRing][2]
+    std::atomic<unsigned> ring_next{0};
+    long long* d_stats = nullptr;
+    sim_render_config rcfg{8, 4, 1, 0, 64, 4, 0};
+    // staging for sim_env_step
+    float* d_cmd = nullptr;
+    float* d_depth = nullptr;
+    uint8_t* d_rgb = nullptr;
+    int stage_n = 0;
+    size_t stage_bytes = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int ctx_alloc(sim_ctx* c, size_t bytes, void** out) {
+    *out = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (c->budget && c->used + bytes > c->budget)
+        return fail(SIM_ERR_BUDGET, "memory budget exceeded: need " + std::to_string(bytes) + " B, used " +
+                                        std::to_string(c->used) + " of " + std::to_string(c->budget));
+    cudaError_t e = cudaMalloc(out, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return cuda_fail(e, "cudaMalloc");
+    }
+    c->used += bytes;
+    return SIM_OK;
+}
+void ctx_free(sim_ctx* c, void* p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    if (bytes == 0) bytes = 16;
+    c->used -= bytes;
+}
+
+bool finite3(const float* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+// Derived constants of the dynamics and the camera, in double then rounded.
+int derive(const sim_params& p, DynConsts& d, CamConsts& cam) {
+    if (!(p.mass > 0) || !(p.J[0] > 0 && p.J[1] > 0 && p.J[2] > 0) || !(p.arm > 0) || !(p.dt > 0) ||
+        p.n_sub < 1 || p.n_sub > kMaxSub || (p.integrator != 0 && p.integrator != 1) || p.width < 1 ||
+        p.height < 1 || p.width > 1024 || p.height > 1024 || !(p.fov_deg > 0 && p.fov_deg < 180) ||
+        !(p.max_depth > 0) || !(p.omega_max >= p.omega_min) || !(p.c_lag >= 0) || !finite3(p.cam_off) ||
+        (p.k[2] == 0 && p.k[1] == 0) || p.k[2] < 0 || p.k[1] < 0)
+        return fail(SIM_ERR_INVALID_ARG, "invalid sim_params");
+    memset(&d, 0, sizeof(d));
+    d.mass = p.mass;
+    d.inv_mass = (float)(1.0 / p.mass);
+    for (int j = 0; j < 3; ++j) {
+        d.J[j] = p.J[j];
+        d.invJ[j] = (float)(1.0 / p.J[j]);
+        d.JK[j] = (float)((double)p.J[j] * p.K_rate[j]);
+        d.rate_max[j] = p.rate_max[j];
+        d.drag[j] = (float)(0.5 * p.rho * p.Cd[j] * p.area[j]);
+    }
+    d.half_a_max_m = (float)(0.5 * (double)p.a_max * p.mass);
+    double A[4][4], rx[4], ry[4], sp[4];
+    for (int i = 0; i < 4; ++i) {
+        const double th = (45.0 + 90.0 * i) * M_PI / 180.0;
+        rx[i] = p.arm * std::cos(th);
+        ry[i] = p.arm * std::sin(th);
+        sp[i] = (i % 2 == 0) ? 1.0 : -1.0;
+        A[0][i] = 1.0;
+        A[1][i] = ry[i];
+        A[2][i] = -rx[i];
+        A[3][i] = sp[i] * p.kappa;
+        d.mix[0][i] = (float)ry[i];
+        d.mix[1][i] = (float)(-rx[i]);
+        d.mix[2][i] = (float)(sp[i] * p.kappa);
+    }
+    // inverse by Gauss-Jordan with partial pivoting
+    double M[4][8];
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 8; ++c) M[r][c] = c < 4 ? A[r][c] : (c - 4 == r ? 1.0 : 0.0);
+    for (int col = 0; col < 4; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 4; ++r)
+            if (std::fabs(M[r][col]) > std::fabs(M[piv][col])) piv = r;
+        if (std::fabs(M[piv][col]) < 1e-12) return fail(SIM_ERR_INVALID_ARG, "singular mixer (kappa = 0?)");
+        if (piv != col)
+            for (int c = 0; c < 8; ++c) std::swap(M[col][c], M[piv][c]);
+        const double inv = 1.0 / M[col][col];
+        for (int c = 0; c < 8; ++c) M[col][c] *= inv;
+        for (int r = 0; r < 4; ++r) {
+            if (r == col) continue;
+            const double f = M[r][col];
+            for (int c = 0; c < 8; ++c) M[r][c] -= f * M[col][c];
+        }
+    }
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            d.Ainv[r][c] = (float)M[r][4 + c];
+            d.dAinv[r][c] = M[r][4 + c];
+        }
+    for (int j = 0; j < 3; ++j) {
+        d.dJ[j] = p.J[j];
+        d.dJK[j] = (double)p.J[j] * p.K_rate[j];
+        d.drate_max[j] = p.rate_max[j];
+        d.dk[j] = p.k[j];
+    }
+    d.dhalf_a_max_m = 0.5 * (double)p.a_max * p.mass;
+    d.domega_min = p.omega_min;
+    d.domega_max = p.omega_max;
+    d.k0 = p.k[0];
+    d.k1 = p.k[1];
+    d.k2 = p.k[2];
+    auto thrust = [&](double w) { return (double)p.k[2] * w * w + (double)p.k[1] * w + (double)p.k[0]; };
+    d.f_lo = (float)thrust(p.omega_min);
+    d.f_hi = (float)thrust(p.omega_max);
+    d.df_lo = thrust(p.omega_min);
+    d.df_hi = thrust(p.omega_max);
+    d.omega_min = p.omega_min;
+    d.omega_max = p.omega_max;
+    const double h = (double)p.dt / p.n_sub;
+    d.h = (float)h;
+    d.decay = (float)std::exp(-(double)p.c_lag * h);
+    d.g = p.g;
+    d.n_sub = p.n_sub;
+    d.integrator = p.integrator;
+    cam.W = p.width;
+    cam.H = p.height;
+    cam.pix = (float)(2.0 * std::tan(0.5 * (double)p.fov_deg * M_PI / 180.0) / p.width);
+    cam.max_depth = p.max_depth;
+    for (int j = 0; j < 3; ++j) cam.cam_off[j] = p.cam_off[j];
+    return SIM_OK;
+}
+
+int upload_table(sim_ctx* c) {
+    const int n = (int)c->scenes.size();
+    if (n > c->table_cap) {
+        int cap = c->table_cap ? c->table_cap : 16;
+        while (cap < n) cap *= 2;
+        void* p;
+        int rc = ctx_alloc(c, sizeof(SceneRow) * cap, &p);
+        if (rc) return rc;
+        ctx_free(c, c->d_table, sizeof(SceneRow) * c->table_cap);
+        c->d_table = (SceneRow*)p;
+        c->table_cap = cap;
+    }
+    std::vector<SceneRow> rows(n);
+    for (int i = 0; i < n; ++i) {
+        const SceneRec& s = c->scenes[i];
+        SceneRow& r = rows[i];
+        memset(&r, 0, sizeof(r));
+        r.live = s.live ? 1 : 0;
+        if (!s.live) {
+            r.root = kEmptyRoot;
+            continue;
+        }
+        r.nodes = s.r.nodes;
+        r.tris = s.r.tris;
+        r.large = s.r.large;
+        r.colors = s.r.colors;
+        r.root = s.r.root;
+        r.n_large = s.r.n_large;
+        r.depth = s.r.depth;
+    }
+    if (n) {
+        cudaError_t e = cudaMemcpy(c->d_table, rows.data(), sizeof(SceneRow) * n, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "scene table upload");
+    }
+    return SIM_OK;
+}
+
+int max_scene_depth(const sim_ctx* c) {
+    int d = 0;
+    for (const auto& s : c->scenes)
+        if (s.live) d = std::max(d, s.r.depth);
+    return d;
+}
+
+struct AllocCtx {
+    sim_ctx* c;
+    SceneRec* rec;
+    int64_t n_tris;
+    int status;
+};
+
+cudaError_t scene_alloc(void* user, LbvhResult* r) {
+    AllocCtx* a = (AllocCtx*)user;
+    const size_t sz[4] = {(size_t)r->n_nodes * 64, (size_t)r->n_bvh * 48, (size_t)r->n_large * 48,
+                          (size_t)a->n_tris * 4};
+    for (int i = 0; i < 4; ++i) {
+        int rc = ctx_alloc(a->c, sz[i], &a->rec->mem[i]);
+        if (rc) {
+            a->status = rc;
+            return cudaErrorMemoryAllocation;
+        }
+        a->rec->bytes += sz[i] ? sz[i] : 16;
+    }
+    r->nodes = (float4*)a->rec->mem[0];
+    r->tris = (float4*)a->rec->mem[1];
+    r->large = (float4*)a->rec->mem[2];
+    r->colors = (uint32_t*)a->rec->mem[3];
+    return cudaSuccess;
+}
+
+void free_scene(sim_ctx* c, SceneRec& s) {
+    const size_t sz[4] = {(size_t)s.r.n_nodes * 64, (size_t)s.r.n_bvh * 48, (size_t)s.r.n_large * 48,
+                          (size_t)s.n_tris * 4};
+    for (int i = 0; i < 4; ++i) {
+        if (s.mem[i]) ctx_free(c, s.mem[i], sz[i]);
+        s.mem[i] = nullptr;
+    }
+    s.live = false;
+    s.bytes = 0;
+}
+
+RenderArgs render_args(sim_ctx* c, int n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb,
+                       int32_t* hit) {
+    RenderArgs a;
+    a.n_agents = n;
+    a.scene_of_agent = soa;
+    a.state = state;
+    a.depth = depth;
+    a.rgb = rgb;
+    a.hit_id = hit;
+    a.table = c->d_table;
+    a.n_scenes = (int)c->scenes.size();
+    a.cam = c->cam;
+    const unsigned slot = c->ring_next.fetch_add(1) % kRing;
+    a.counter = c->d_ring + 2 * slot;
+    a.done = c->d_ring + 2 * slot + 1;
+    a.err = c->d_err;
+    a.counters = c->d_stats;
+    return a;
+}
+
+int check_render_args(sim_ctx* c, int n, const void* soa, const void* state) {
+    if (!c) return fail(SIM_ERR_INVALID_ARG, "null context");
+    if (n < 0) return fail(SIM_ERR_INVALID_ARG, "negative agent count");
+    if (n > 0 && (!soa || !state)) return fail(SIM_ERR_INVALID_ARG, "null scene_of_agent or state");
+    const long long tiles = (long long)((c->cam.W + 7) / 4) * ((c->cam.H + 7) / 2);
+    if ((long long)n * tiles >= (1ll << 31)) return fail(SIM_ERR_INVALID_ARG, "too many agents for one launch");
+    if (max_scene_depth(c) >= c->rcfg.stack_depth)
+        return fail(SIM_ERR_INVALID_ARG, "a scene BVH is deeper than the traversal stack");
+    return SIM_OK;
+}
+
+int do_render(sim_ctx* c, int n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb, int32_t* hit,
+              bool count, const sim_render_config& cfg, cudaStream_t s) {
+    if (n == 0) return SIM_OK;
+    RenderArgs a = render_args(c, n, soa, state, depth, rgb, hit);
+    int ctas = 0;
+    if (cfg.ctas_per_sm > 0) ctas = cfg.ctas_per_sm * c->num_sms;
+    cudaError_t e = launch_render(a, cfg, ctas, count, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ray-cast launch");
+    return SIM_OK;
+}
+
+}  // namespace
+
+namespace vf {
+cudaError_t launch_cfg(const void* kernel, const RenderArgs& a, int warps_per_cta, int ctas, size_t smem,
+                       cudaStream_t s) {
+    int dev;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ctas <= 0) {
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * warps_per_cta, smem);
+        if (e != cudaSuccess) return e;
+        ctas = std::max(1, per_sm) * sms;
+    }
+    // never more CTAs than work items need
+    const int tiles = ((a.cam.W + 3) / 4) * ((a.cam.H + 1) / 2);  // upper bound over tile shapes
+    const long long items = (long long)a.n_agents * tiles;
+    const long long need = (items + warps_per_cta - 1) / warps_per_cta;
+    if (need < ctas) ctas = (int)std::max(1ll, need);
+    void* args[] = {(void*)&a};
+    return cudaLaunchKernel(kernel, dim3(ctas), dim3(32 * warps_per_cta), args, smem, s);
+}
+}  // namespace vf
+
+extern "C" {
+
+const char* sim_version(void) { return "visfly_b300 0.1 (sm_103a)"; }
+
+const char* sim_last_error(const sim_ctx*) { return g_err.c_str(); }
+
+int sim_create_ctx(sim_ctx** out, int device, const sim_params* p, size_t mem_budget_bytes) {
+    if (!out || !p) return fail(SIM_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(SIM_ERR_INVALID_ARG, "no such device");
+    sim_ctx* c = new sim_ctx();
+    c->device = device;
+    c->budget = mem_budget_bytes;
+    int rc = derive(*p, c->dyn, c->cam);
+    if (rc) {
+        delete c;
+        return rc;
+    }
+    c->params = *p;
+    DeviceGuard g(device);
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    void *err, *ring, *stats;
+    if ((rc = ctx_alloc(c, sizeof(int), &err)) || (rc = ctx_alloc(c, sizeof(unsigned) * 2 * kRing, &ring)) ||
+        (rc = ctx_alloc(c, sizeof(long long) * 8, &stats))) {
+        sim_destroy_ctx(c);
+        return rc;
+    }
+    c->d_err = (int*)err;
+    c->d_ring = (unsigned*)ring;
+    c->d_stats = (long long*)stats;
+    cudaMemset(c->d_err, 0, sizeof(int));
+    cudaMemset(c->d_ring, 0, sizeof(unsigned) * 2 * kRing);
+    cudaMemset(c->d_stats, 0, sizeof(long long) * 8);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        sim_destroy_ctx(c);
+        return cuda_fail(e, "context set-up");
+    }
+    *out = c;
+    return SIM_OK;
+}
+
+int sim_destroy_ctx(sim_ctx* c) {
+    if (!c) return SIM_OK;
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    for (auto& s : c->scenes)
+        if (s.live) free_scene(c, s);
+    ctx_free(c, c->d_table, sizeof(SceneRow) * c->table_cap);
+    ctx_free(c, c->d_err, sizeof(int));
+    ctx_free(c, c->d_ring, sizeof(unsigned) * 2 * kRing);
+    ctx_free(c, c->d_stats, sizeof(long long) * 8);
+    ctx_free(c, c->d_cmd, 0);
+    ctx_free(c, c->d_depth, 0);
+    ctx_free(c, c->d_rgb, 0);
+    delete c;
+    return SIM_OK;
+}
+
+int sim_set_params(sim_ctx* c, const sim_params* p) {
+    if (!c || !p) return fail(SIM_ERR_INVALID_ARG, "null argument");
+    DynConsts d;
+    CamConsts cam;
+    int rc = derive(*p, d, cam);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->params = *p;
+    c->dyn = d;
+    c->cam = cam;
+    return SIM_OK;
+}
+
+int sim_create_scene(sim_ctx* c, const float* verts, int64_t n_verts, const int32_t* tris, int64_t n_tris,
+                     const uint8_t* rgb, int32_t* scene_id_out, void* stream) {
+    if (!c || !scene_id_out) return fail(SIM_ERR_INVALID_ARG, "null argument");
+    *scene_id_out = -1;
+    if (n_verts < 0 || n_tris < 0 || n_tris > (1ll << 27) || n_verts > (1ll << 31))
+        return fail(SIM_ERR_INVALID_ARG, "bad mesh size");
+    if ((n_verts > 0 && !verts) || (n_tris > 0 && (!tris || !rgb)))
+        return fail(SIM_ERR_INVALID_ARG, "null mesh array");
+    for (int64_t i = 0; i < 3 * n_tris; ++i)
+        if (tris[i] < 0 || tris[i] >= n_verts) return fail(SIM_ERR_INVALID_ARG, "triangle index out of range");
+    for (int64_t i = 0; i < 3 * n_verts; ++i)
+        if (!std::isfinite(verts[i])) return fail(SIM_ERR_INVALID_ARG, "non-finite vertex");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    SceneRec rec;
+    rec.n_tris = n_tris;
+    const size_t vb = sizeof(float) * 3 * std::max<int64_t>(n_verts, 1);
+    const size_t tb = sizeof(int32_t) * 3 * std::max<int64_t>(n_tris, 1);
+    const size_t cb = 3 * std::max<int64_t>(n_tris, 1);
+    const size_t sb = lbvh_scratch_bytes(n_tris);
+    void *dv = nullptr, *dt = nullptr, *dc = nullptr, *ds = nullptr;
+    int rc;
+    if ((rc = ctx_alloc(c, vb, &dv)) || (rc = ctx_alloc(c, tb, &dt)) || (rc = ctx_alloc(c, cb, &dc)) ||
+        (rc = ctx_alloc(c, sb, &ds))) {
+        ctx_free(c, dv, vb);
+        ctx_free(c, dt, tb);
+        ctx_free(c, dc, cb);
+        ctx_free(c, ds, sb);
+        return rc;
+    }
+    auto cleanup = [&]() {
+        ctx_free(c, dv, vb);
+        ctx_free(c, dt, tb);
+        ctx_free(c, dc, cb);
+        ctx_free(c, ds, sb);
+    };
+    cudaError_t e = cudaSuccess;
+    if (n_verts) e = cudaMemcpyAsync(dv, verts, sizeof(float) * 3 * n_verts, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_tris) e = cudaMemcpyAsync(dt, tris, sizeof(int32_t) * 3 * n_tris, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_tris) e = cudaMemcpyAsync(dc, rgb, 3 * n_tris, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "mesh upload");
+    }
+    AllocCtx ac{c, &rec, n_tris, SIM_OK};
+    if (n_tris == 0) {
+        rec.r = LbvhResult{};
+        rec.r.root = kEmptyRoot;
+        e = scene_alloc(&ac, &rec.r);
+    } else {
+        e = lbvh_build(n_tris, (const float*)dv, (const int*)dt, (const uint8_t*)dc, ds, scene_alloc, &ac, &rec.r, s);
+    }
+    cleanup();
+    if (e != cudaSuccess) {
+        for (int i = 0; i < 4; ++i) {
+            const size_t sz[4] = {(size_t)rec.r.n_nodes * 64, (size_t)rec.r.n_bvh * 48, (size_t)rec.r.n_large * 48,
+                                  (size_t)n_tris * 4};
+            if (rec.mem[i]) ctx_free(c, rec.mem[i], sz[i]);
+        }
+        if (ac.status) return ac.status;
+        return cuda_fail(e, "BVH build");
+    }
+    rec.live = true;
+    int id = -1;
+    for (int i = 0; i < (int)c->scenes.size(); ++i)
+        if (!c->scenes[i].live) {
+            id = i;
+            break;
+        }
+    if (id < 0) {
+        id = (int)c->scenes.size();
+        c->scenes.push_back(rec);
+    } else {
+        c->scenes[id] = rec;
+    }
+    rc = upload_table(c);
+    if (rc) {
+        free_scene(c, c->scenes[id]);
+        return rc;
+    }
+    *scene_id_out = id;
+    return SIM_OK;
+}
+
+int sim_destroy_scene(sim_ctx* c, int32_t id) {
+    if (!c) return fail(SIM_ERR_INVALID_ARG, "null context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (id < 0 || id >= (int)c->scenes.size() || !c->scenes[id].live) return fail(SIM_ERR_NOT_FOUND, "no such scene");
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    free_scene(c, c->scenes[id]);
+    return upload_table(c);
+}
+
+int sim_scene_info_get(const sim_ctx* c, int32_t id, sim_scene_info* info) {
+    if (!c || !info) return fail(SIM_ERR_INVALID_ARG, "null argument");
+    if (id < 0 || id >= (int)c->scenes.size() || !c->scenes[id].live) return fail(SIM_ERR_NOT_FOUND, "no such scene");
+    const SceneRec& s = c->scenes[id];
+    info->n_tris = s.n_tris;
+    info->n_nodes = s.r.n_nodes;
+    info->n_large = s.r.n_large;
+    info->depth = s.r.depth;
+    info->leaf_max = kLeafMax;
+    info->bytes = (int64_t)s.bytes;
+    return SIM_OK;
+}
+
+int sim_step(sim_ctx* c, int32_t n, float* state, const float* cmd, float* ckpt, void* stream) {
+    if (!c || n < 0 || (n > 0 && (!state || !cmd))) return fail(SIM_ERR_INVALID_ARG, "bad sim_step arguments");
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_step(c->dyn, n, state, cmd, ckpt, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e, "sim_step launch");
+}
+
+int sim_step_backward(sim_ctx* c, int32_t n, const float* state_in, const float* cmd, const float* g_out,
+                      float* g_in, float* g_cmd, void* stream) {
+    if (!c || n < 0 || (n > 0 && (!state_in || !cmd || !g_out || !g_in || !g_cmd)))
+        return fail(SIM_ERR_INVALID_ARG, "bad sim_step_backward arguments");
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_step_backward(c->dyn, n, state_in, cmd, g_out, g_in, g_cmd, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e, "sim_step_backward launch");
+}
+
+int sim_rollout(sim_ctx* c, int32_t n, int32_t T, int32_t K, const float* state0, const float* cmds, float* states_out,
+                float* ckpt, float* state_final, void* stream) {
+    if (!c || n < 0 || T < 0 || K < 1 || (n > 0 && (!state0 || (T > 0 && !cmds))))
+        return fail(SIM_ERR_INVALID_ARG, "bad sim_rollout arguments");
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_rollout(c->dyn, n, T, K, state0, cmds, states_out, ckpt, state_final, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e, "sim_rollout launch");
+}
+
+int sim_rollout_backward(sim_ctx* c, int32_t n, int32_t T, int32_t K, const float* ckpt, const float* cmds,
+                         const float* g_states, float* g_state0, float* g_cmds, void* stream) {
+    if (!c || n < 0 || T < 1 || K < 1 || K > kMaxCkptK ||
+        (n > 0 && (!ckpt || !cmds || !g_states || !g_state0 || !g_cmds)))
+        return fail(SIM_ERR_INVALID_ARG, "bad sim_rollout_backward arguments");
+    DeviceGuard g(c->device);
+    cudaError_t e =
+        launch_rollout_backward(c->dyn, n, T, K, ckpt, cmds, g_states, g_state0, g_cmds, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e, "sim_rollout_backward launch");
+}
+
+int sim_render(sim_ctx* c, int32_t n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb,
+               int32_t* hit, void* stream) {
+    int rc = check_render_args(c, n, soa, state);
+    if (rc) return rc;
+    DeviceGuard g(c->device);
+    return do_render(c, n, soa, state, depth, rgb, hit, false, c->rcfg, (cudaStream_t)stream);
+}
+
+int sim_render_counted(sim_ctx* c, int32_t n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb,
+                       int32_t* hit, sim_render_counters* out, void* stream) {
+    int rc = check_render_args(c, n, soa, state);
+    if (rc) return rc;
+    if (!out) return fail(SIM_ERR_INVALID_ARG, "null counters");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(c->d_stats, 0, sizeof(long long) * 8, s);
+    if (e != cudaSuccess) return cuda_fail(e, "counter reset");
+    rc = do_render(c, n, soa, state, depth, rgb, hit, true, c->rcfg, s);
+    if (rc) return rc;
+    long long h[8];
+    e = cudaMemcpyAsync(h, c->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "counter read");
+    out->node_visits = h[0];
+    out->tri_tests = h[1];
+    out->large_tests = h[2];
+    out->items = h[3];
+    out->rays = (int64_t)n * c->cam.W * c->cam.H;
+    return SIM_OK;
+}
+
+int sim_render_scene(sim_ctx* c, int32_t n, int32_t scene_id, const float* state, float* depth, uint8_t* rgb,
+                     int32_t* hit, void* stream) {
+    // a device array of n copies of scene_id is needed; keep a small cache in the context staging area
+    if (!c) return fail(SIM_ERR_INVALID_ARG, "null context");
+    if (scene_id < 0 || scene_id >= (int)c->scenes.size() || !c->scenes[scene_id].live)
+        return fail(SIM_ERR_NOT_FOUND, "no such scene");
+    if (n <= 0) return n == 0 ? SIM_OK : fail(SIM_ERR_INVALID_ARG, "negative agent count");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    void* p;
+    int rc = ctx_alloc(c, sizeof(int32_t) * n, &p);
+    if (rc) return rc;
+    std::vector<int32_t> ids(n, scene_id);
+    cudaError_t e = cudaMemcpyAsync(p, ids.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        ctx_free(c, p, sizeof(int32_t) * n);
+        return cuda_fail(e, "scene id upload");
+    }
+    rc = sim_render(c, n, (const int32_t*)p, state, depth, rgb, hit, stream);
+    cudaStreamSynchronize(s);
+    ctx_free(c, p, sizeof(int32_t) * n);
+    return rc;
+}
+
+int sim_env_step(sim_ctx* c, int32_t n, const int32_t* soa, float* state, const float* cmd_host, float* depth_host,
+                 uint8_t* rgb_host, float* state_host, void* stream) {
+    if (!c || n < 0 || (n > 0 && (!soa || !state || !cmd_host)))
+        return fail(SIM_ERR_INVALID_ARG, "bad sim_env_step arguments");
+    if (n == 0) return SIM_OK;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t px = (size_t)n * c->cam.W * c->cam.H;
+    if (n > c->stage_n) {
+        cudaStreamSynchronize(s);
+        ctx_free(c, c->d_cmd, sizeof(float) * 4 * c->stage_n);
+        ctx_free(c, c->d_depth, sizeof(float) * c->stage_bytes);
+        ctx_free(c, c->d_rgb, 3 * c->stage_bytes);
+        c->d_cmd = nullptr;
+        c->d_depth = nullptr;
+        c->d_rgb = nullptr;
+        c->stage_n = 0;
+        c->stage_bytes = 0;
+        void *a, *b, *d;
+        int rc;
+        if ((rc = ctx_alloc(c, sizeof(float) * 4 * n, &a))) return rc;
+        if ((rc = ctx_alloc(c, sizeof(float) * px, &b))) {
+            ctx_free(c, a, sizeof(float) * 4 * n);
+            return rc;
+        }
+        if ((rc = ctx_alloc(c, 3 * px, &d))) {
+            ctx_free(c, a, sizeof(float) * 4 * n);
+            ctx_free(c, b, sizeof(float) * px);
+            return rc;
+        }
+        c->d_cmd = (float*)a;
+        c->d_depth = (float*)b;
+        c->d_rgb = (uint8_t*)d;
+        c->stage_n = n;
+        c->stage_bytes = px;
+    }
+    cudaError_t e = cudaMemcpyAsync(c->d_cmd, cmd_host, sizeof(float) * 4 * n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "command upload");
+    int rc = sim_step(c, n, state, c->d_cmd, nullptr, stream);
+    if (rc) return rc;
+    rc = sim_render(c, n, soa, state, depth_host ? c->d_depth : nullptr, rgb_host ? c->d_rgb : nullptr, nullptr, stream);
+    if (rc) return rc;
+    if (depth_host) e = cudaMemcpyAsync(depth_host, c->d_depth, sizeof(float) * px, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && rgb_host) e = cudaMemcpyAsync(rgb_host, c->d_rgb, 3 * px, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && state_host)
+        e = cudaMemcpyAsync(state_host, state, sizeof(float) * 17 * n, cudaMemcpyDeviceToHost, s);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e, "observation download");
+}
+
+int sim_get_render_config(const sim_ctx* c, sim_render_config* cfg) {
+    if (!c || !cfg) return fail(SIM_ERR_INVALID_ARG, "null argument");
+    *cfg = c->rcfg;
+    return SIM_OK;
+}
+
+int sim_set_render_config(sim_ctx* c, const sim_render_config* cfg) {
+    if (!c || !cfg) return fail(SIM_ERR_INVALID_ARG, "null argument");
+    if (!render_config_valid(*cfg)) return fail(SIM_ERR_INVALID_ARG, "unsupported render configuration");
+    c->rcfg = *cfg;
+    return SIM_OK;
+}
+
+int sim_render_config_list(sim_render_config* out, int32_t max) { return render_config_list(out, max); }
+
+int sim_autotune_render(sim_ctx* c, int32_t n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb,
+                        int32_t iters, sim_render_config* best, float* times_ms, int32_t max_times, void* stream) {
+    int rc = check_render_args(c, n, soa, state);
+    if (rc) return rc;
+    if (iters < 1 || !best) return fail(SIM_ERR_INVALID_ARG, "bad autotune arguments");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    sim_render_config cfgs[64];
+    const int nc = render_config_list(cfgs, 64);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    int best_i = -1;
+    const int need_depth = max_scene_depth(c);
+    for (int i = 0; i < nc; ++i) {
+        sim_render_config cf = cfgs[i];
+        if (need_depth >= cf.stack_depth) continue;
+        rc = do_render(c, n, soa, state, depth, rgb, nullptr, false, cf, s);  // warm-up
+        if (rc) break;
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < iters && !rc; ++k) rc = do_render(c, n, soa, state, depth, rgb, nullptr, false, cf, s);
+        cudaEventRecord(e1, s);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (rc) break;
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "autotune timing");
+            break;
+        }
+        float ms;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= iters;
+        if (times_ms && i < max_times) times_ms[i] = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_i = i;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (best_i < 0) return fail(SIM_ERR_INVALID_ARG, "no configuration fits the scene depth");
+    c->rcfg = cfgs[best_i];
+    *best = cfgs[best_i];
+    return SIM_OK;
+}
+
+int sim_get_status(sim_ctx* c, void* stream, int32_t timeout_ms) {
+    if (!c) return fail(SIM_ERR_INVALID_ARG, "null context");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t q = cudaStreamQuery(s);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return cuda_fail(q, "stream");
+        if (timeout_ms >= 0 &&
+            std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms))
+            return fail(SIM_ERR_TIMEOUT, "stream still busy after timeout");
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "error word");
+    if (h == kDevErrTraversal) return fail(SIM_ERR_TRAVERSAL, "device: traversal stack overflow or iteration cap");
+    if (h == kDevErrNotFound) return fail(SIM_ERR_NOT_FOUND, "device: agent refers to an unknown scene");
+    if (h != 0) return fail(SIM_ERR_CUDA, "device error word " + std::to_string(h));
+    return SIM_OK;
+}
+
+int sim_mem_usage(const sim_ctx* c, size_t* used, size_t* budget) {
+    if (!c) return fail(SIM_ERR_INVALID_ARG, "null context");
+    if (used) *used = c->used;
+    if (budget) *budget = c->budget;
+    return SIM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+__global__ void probe_read_kernel(const float4* __restrict__ buf, size_t n4, int iters, float* sink) {
+    float acc = 0.0f;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (int it = 0; it < iters; ++it)
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+            const float4 v = __ldcg(buf + i);
+            acc += v.x + v.y + v.z + v.w;
+        }
+    if (acc == 1234.5678f) *sink = acc;
+}
+}  // namespace
+
+extern "C" int sim_probe_read_bandwidth(sim_ctx* c, size_t bytes, int32_t iters, double* gbs, void* stream) {
+    if (!c || !gbs || bytes < 4096 || iters < 1) return fail(SIM_ERR_INVALID_ARG, "bad probe arguments");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    void* buf;
+    int rc = ctx_alloc(c, bytes + 256, &buf);
+    if (rc) return rc;
+    const size_t n4 = bytes / 16;
+    cudaMemsetAsync(buf, 0, bytes + 256, s);
+    const int grid = c->num_sms * 8;
+    probe_read_kernel<<<grid, 512, 0, s>>>((const float4*)buf, n4, 1, (float*)((char*)buf + bytes));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    probe_read_kernel<<<grid, 512, 0, s>>>((const float4*)buf, n4, iters, (float*)((char*)buf + bytes));
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx_free(c, buf, bytes + 256);
+    if (e != cudaSuccess) return cuda_fail(e, "probe");
+    *gbs = (double)n4 * 16.0 * iters / (ms * 1e-3) / 1e9;
+    return SIM_OK;
+}

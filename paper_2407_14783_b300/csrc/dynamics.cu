@@ -1,0 +1,570 @@
+// Quadrotor dynamics and its adjoint, one thread per agent (sm_103a, FP32).
+//
+// Forward step (Sec. III-A): body-rate (CTBR) controller -> rotor first-order
+// lag (Eq. 4, exact over the sub-step) -> rotor thrusts, collective thrust and
+// moment (Eq. 3, 4) held over the sub-step -> RK4 (or Euler) on Eq. 1 with
+// body-frame quadratic drag (Eq. 2) -> quaternion normalisation.
+//
+// Adjoint: hand-derived reverse mode of the same map.  Each thread recomputes
+// its agent's forward internals (stage states, clamp flags) and sweeps them
+// backwards; the rollout adjoint re-runs K steps from a checkpoint, keeps them
+// in thread-local memory and walks them in reverse.
+//
+// Layout: state SoA float32 [17][n], commands [4][n]; loads and stores are
+// coalesced across the agents of a warp.
+#include "common.cuh"
+#include "launch.h"
+
+namespace vf {
+namespace {
+
+__device__ __forceinline__ void cross3(const float a[3], const float b[3], float c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Body-to-world rotation of q / |q| (q = w, x, y, z); also returns 1/|q|^2.
+__device__ __forceinline__ void rotation(const float q[4], float R[3][3], float& inv_n) {
+    const float w = q[0], x = q[1], y = q[2], z = q[3];
+    inv_n = 1.0f / (w * w + x * x + y * y + z * z);
+    R[0][0] = (w * w + x * x - y * y - z * z) * inv_n;
+    R[0][1] = 2.0f * (x * y - w * z) * inv_n;
+    R[0][2] = 2.0f * (x * z + w * y) * inv_n;
+    R[1][0] = 2.0f * (x * y + w * z) * inv_n;
+    R[1][1] = (w * w - x * x + y * y - z * z) * inv_n;
+    R[1][2] = 2.0f * (y * z - w * x) * inv_n;
+    R[2][0] = 2.0f * (x * z - w * y) * inv_n;
+    R[2][1] = 2.0f * (y * z + w * x) * inv_n;
+    R[2][2] = (w * w - x * x - y * y + z * z) * inv_n;
+}
+
+// Controller internals kept for the adjoint.
+struct CtrlTape {
+    float fc[4];      // clamped rotor thrust requests
+    float dw_df[4];   // slope of the thrust inverse at fc
+    bool in_f[4];     // thrust request inside [f_lo, f_hi]
+    bool in_w[4];     // rotor speed inside [omega_min, omega_max]
+};
+
+// CTBR: u0 -> collective thrust m a, u1..3 -> desired rates; P rate loop with
+// gyroscopic feed-forward -> desired moment; mixer inverse -> rotor thrusts,
+// clamped to the reachable range -> desired rotor speeds.  Evaluated in FP64
+// (a few dozen operations per agent and sub-step; see DynConsts).
+__device__ __forceinline__ void controller(const DynConsts& c, const float Om_f[3], const float u[4],
+                                           float omega_des[4], CtrlTape* tape) {
+    const double Om[3] = {Om_f[0], Om_f[1], Om_f[2]};
+    const double L[3] = {c.dJ[0] * Om[0], c.dJ[1] * Om[1], c.dJ[2] * Om[2]};
+    const double gyro[3] = {Om[1] * L[2] - Om[2] * L[1], Om[2] * L[0] - Om[0] * L[2], Om[0] * L[1] - Om[1] * L[0]};
+    double rhs[4];
+    rhs[0] = ((double)u[0] + 1.0) * c.dhalf_a_max_m;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) rhs[j + 1] = c.dJK[j] * ((double)u[j + 1] * c.drate_max[j] - Om[j]) + gyro[j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const double f = c.dAinv[i][0] * rhs[0] + c.dAinv[i][1] * rhs[1] + c.dAinv[i][2] * rhs[2] +
+                         c.dAinv[i][3] * rhs[3];
+        const bool in_f = f >= c.df_lo && f <= c.df_hi;
+        const double fc = fmin(fmax(f, c.df_lo), c.df_hi);
+        double w, dw;
+        if (c.dk[2] != 0.0) {
+            const double disc = c.dk[1] * c.dk[1] - 4.0 * c.dk[2] * (c.dk[0] - fc);
+            const double sq = sqrt(fmax(disc, 0.0));
+            w = (sq - c.dk[1]) / (2.0 * c.dk[2]);
+            dw = disc > 0.0 ? 1.0 / sq : 0.0;
+        } else {
+            w = (fc - c.dk[0]) / c.dk[1];
+            dw = 1.0 / c.dk[1];
+        }
+        const bool in_w = w >= c.domega_min && w <= c.domega_max;
+        omega_des[i] = (float)fmin(fmax(w, c.domega_min), c.domega_max);
+        if (tape) {
+            tape->fc[i] = (float)fc;
+            tape->dw_df[i] = (float)dw;
+            tape->in_f[i] = in_f;
+            tape->in_w[i] = in_w;
+        }
+    }
+}
+
+// Eq. 1 right-hand side for y = (x, v, q, Omega) with body thrust (0,0,Fz) and
+// moment eta fixed; drag d = -rho Cd s / 2 * v_B |v_B| per body axis (Eq. 2).
+__device__ __forceinline__ void rhs(const DynConsts& c, const float y[13], float Fz, const float eta[3],
+                                    float dy[13]) {
+    const float* v = y + 3;
+    const float* q = y + 6;
+    const float* Om = y + 10;
+    float R[3][3], inv_n;
+    rotation(q, R, inv_n);
+    float fB[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float vb = R[0][j] * v[0] + R[1][j] * v[1] + R[2][j] * v[2];
+        fB[j] = -c.drag[j] * vb * fabsf(vb);
+    }
+    fB[2] += Fz;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        dy[j] = v[j];
+        dy[3 + j] = (R[j][0] * fB[0] + R[j][1] * fB[1] + R[j][2] * fB[2]) * c.inv_mass;
+    }
+    dy[5] -= c.g;
+    dy[6] = 0.5f * (-q[1] * Om[0] - q[2] * Om[1] - q[3] * Om[2]);
+    dy[7] = 0.5f * (q[0] * Om[0] + q[2] * Om[2] - q[3] * Om[1]);
+    dy[8] = 0.5f * (q[0] * Om[1] - q[1] * Om[2] + q[3] * Om[0]);
+    dy[9] = 0.5f * (q[0] * Om[2] + q[1] * Om[1] - q[2] * Om[0]);
+    float L[3] = {c.J[0] * Om[0], c.J[1] * Om[1], c.J[2] * Om[2]};
+    float cr[3];
+    cross3(Om, L, cr);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dy[10 + j] = (eta[j] - cr[j]) * c.invJ[j];
+}
+
+// Controller, rotor lag and thrust/moment of one sub-step.
+__device__ __forceinline__ void rotors(const DynConsts& c, float y[17], const float u[4], float& Fz, float eta[3],
+                                       CtrlTape* tape) {
+    float wd[4];
+    controller(c, y + 10, u, wd, tape);
+    Fz = 0.0f;
+    eta[0] = eta[1] = eta[2] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float w = wd[i] + (y[13 + i] - wd[i]) * c.decay;
+        y[13 + i] = w;
+        const float f = (c.k2 * w + c.k1) * w + c.k0;
+        Fz += f;
+        eta[0] += c.mix[0][i] * f;
+        eta[1] += c.mix[1][i] * f;
+        eta[2] += c.mix[2][i] * f;
+    }
+}
+
+__device__ __forceinline__ void substep(const DynConsts& c, float y[17], const float u[4]) {
+    float Fz, eta[3];
+    rotors(c, y, u, Fz, eta, nullptr);
+    const float h = c.h;
+    if (c.integrator == 1) {
+        float k1[13];
+        rhs(c, y, Fz, eta, k1);
+#pragma unroll
+        for (int j = 0; j < 13; ++j) y[j] += h * k1[j];
+    } else {
+        float k[13], acc[13], yt[13];
+        rhs(c, y, Fz, eta, k);
+#pragma unroll
+        for (int j = 0; j < 13; ++j) {
+            acc[j] = k[j];
+            yt[j] = y[j] + 0.5f * h * k[j];
+        }
+        rhs(c, yt, Fz, eta, k);
+#pragma unroll
+        for (int j = 0; j < 13; ++j) {
+            acc[j] += 2.0f * k[j];
+            yt[j] = y[j] + 0.5f * h * k[j];
+        }
+        rhs(c, yt, Fz, eta, k);
+#pragma unroll
+        for (int j = 0; j < 13; ++j) {
+            acc[j] += 2.0f * k[j];
+            yt[j] = y[j] + h * k[j];
+        }
+        rhs(c, yt, Fz, eta, k);
+#pragma unroll
+        for (int j = 0; j < 13; ++j) y[j] += (h / 6.0f) * (acc[j] + k[j]);
+    }
+    const float qn = rsqrtf(y[6] * y[6] + y[7] * y[7] + y[8] * y[8] + y[9] * y[9]);
+#pragma unroll
+    for (int j = 6; j < 10; ++j) y[j] *= qn;
+}
+
+__device__ __forceinline__ void control_step(const DynConsts& c, float y[17], const float u[4]) {
+    for (int s = 0; s < c.n_sub; ++s) substep(c, y, u);
+}
+
+// ---------------------------------------------------------------- adjoint
+// Reverse mode of rhs(): accumulate the cotangents of y, Fz and eta from the
+// cotangent kb of dy.
+__device__ void rhs_vjp(const DynConsts& c, const float y[13], float Fz, const float kb[13], float yb[13],
+                        float& Fzb, float etab[3]) {
+    const float* v = y + 3;
+    const float* q = y + 6;
+    const float* Om = y + 10;
+    float R[3][3], inv_n;
+    rotation(q, R, inv_n);
+    float vB[3], fB[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        vB[j] = R[0][j] * v[0] + R[1][j] * v[1] + R[2][j] * v[2];
+        fB[j] = -c.drag[j] * vB[j] * fabsf(vB[j]);
+    }
+    fB[2] += Fz;
+    // dx = v
+#pragma unroll
+    for (int j = 0; j < 3; ++j) yb[3 + j] += kb[j];
+    // dv = R fB / m - g z
+    const float* kv = kb + 3;
+    float Rb[3][3];
+    float fBb[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        fBb[j] = (R[0][j] * kv[0] + R[1][j] * kv[1] + R[2][j] * kv[2]) * c.inv_mass;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) Rb[i][j] = kv[i] * fB[j] * c.inv_mass;
+    }
+    Fzb += fBb[2];
+    float vBb[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) vBb[j] = fBb[j] * (-2.0f * c.drag[j] * fabsf(vB[j]));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        yb[3 + i] += R[i][0] * vBb[0] + R[i][1] * vBb[1] + R[i][2] * vBb[2];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Rb[i][j] += v[i] * vBb[j];
+    }
+    // dq = 1/2 q (x) (0, Omega)
+    const float h0 = 0.5f * kb[6], h1 = 0.5f * kb[7], h2 = 0.5f * kb[8], h3 = 0.5f * kb[9];
+    float qb[4];
+    qb[0] = h1 * Om[0] + h2 * Om[1] + h3 * Om[2];
+    qb[1] = -h0 * Om[0] - h2 * Om[2] + h3 * Om[1];
+    qb[2] = -h0 * Om[1] + h1 * Om[2] - h3 * Om[0];
+    qb[3] = -h0 * Om[2] - h1 * Om[1] + h2 * Om[0];
+    yb[10] += -h0 * q[1] + h1 * q[0] + h2 * q[3] - h3 * q[2];
+    yb[11] += -h0 * q[2] - h1 * q[3] + h2 * q[0] + h3 * q[1];
+    yb[12] += -h0 * q[3] + h1 * q[2] - h2 * q[1] + h3 * q[0];
+    // dOmega = (eta - Omega x J Omega) / J
+    float cb[3], L[3] = {c.J[0] * Om[0], c.J[1] * Om[1], c.J[2] * Om[2]};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        etab[j] += kb[10 + j] * c.invJ[j];
+        cb[j] = -kb[10 + j] * c.invJ[j];
+    }
+    float t[3], Lb[3];
+    cross3(L, cb, t);   // Omega-bar from Omega in (Omega x L)
+    cross3(cb, Om, Lb); // L-bar
+#pragma unroll
+    for (int j = 0; j < 3; ++j) yb[10 + j] += t[j] + c.J[j] * Lb[j];
+    // R(q) = M(q) / |q|^2
+    const float w = q[0], x = q[1], yy = q[2], z = q[3];
+    float dot = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) dot += Rb[i][j] * R[i][j];
+    const float gw = 2.0f * (w * (Rb[0][0] + Rb[1][1] + Rb[2][2]) + z * (Rb[1][0] - Rb[0][1]) +
+                             yy * (Rb[0][2] - Rb[2][0]) + x * (Rb[2][1] - Rb[1][2]));
+    const float gx = 2.0f * (x * (Rb[0][0] - Rb[1][1] - Rb[2][2]) + yy * (Rb[0][1] + Rb[1][0]) +
+                             z * (Rb[0][2] + Rb[2][0]) + w * (Rb[2][1] - Rb[1][2]));
+    const float gy = 2.0f * (yy * (-Rb[0][0] + Rb[1][1] - Rb[2][2]) + x * (Rb[0][1] + Rb[1][0]) +
+                             w * (Rb[0][2] - Rb[2][0]) + z * (Rb[1][2] + Rb[2][1]));
+    const float gz = 2.0f * (z * (-Rb[0][0] - Rb[1][1] + Rb[2][2]) + w * (Rb[1][0] - Rb[0][1]) +
+                             x * (Rb[0][2] + Rb[2][0]) + yy * (Rb[1][2] + Rb[2][1]));
+    yb[6] += qb[0] + gw * inv_n - 2.0f * w * inv_n * dot;
+    yb[7] += qb[1] + gx * inv_n - 2.0f * x * inv_n * dot;
+    yb[8] += qb[2] + gy * inv_n - 2.0f * yy * inv_n * dot;
+    yb[9] += qb[3] + gz * inv_n - 2.0f * z * inv_n * dot;
+}
+
+// Reverse mode of one sub-step: y_in (pre), u, cotangent gout of the post-sub-
+// step state -> gin (cotangent of y_in) and accumulated gu.
+__device__ void substep_vjp(const DynConsts& c, const float y_in[17], const float u[4], const float gout[17],
+                            float gin[17], float gu[4]) {
+    // forward recompute
+    float y[17];
+#pragma unroll
+    for (int j = 0; j < 17; ++j) y[j] = y_in[j];
+    CtrlTape tape;
+    float Fz, eta[3];
+    rotors(c, y, u, Fz, eta, &tape);
+    const float h = c.h;
+    float ys[4][13];
+    float yn[13];
+    if (c.integrator == 1) {
+        float k1[13];
+#pragma unroll
+        for (int j = 0; j < 13; ++j) ys[0][j] = y[j];
+        rhs(c, ys[0], Fz, eta, k1);
+#pragma unroll
+        for (int j = 0; j < 13; ++j) yn[j] = ys[0][j] + h * k1[j];
+    } else {
+        float k[13], acc[13];
+#pragma unroll
+        for (int j = 0; j < 13; ++j) ys[0][j] = y[j];
+        rhs(c, ys[0], Fz, eta, k);
+#pragma unroll
+        for (int j = 0; j < 13; ++j) {
+            acc[j] = k[j];
+            ys[1][j] = y[j] + 0.5f * h * k[j];
+        }
+        rhs(c, ys[1], Fz, eta, k);
+#pragma unroll
+        for (int j = 0; j < 13; ++j) {
+            acc[j] += 2.0f * k[j];
+            ys[2][j] = y[j] + 0.5f * h * k[j];
+        }
+        rhs(c, ys[2], Fz, eta, k);
+#pragma unroll
+        for (int j = 0; j < 13; ++j) {
+            acc[j] += 2.0f * k[j];
+            ys[3][j] = y[j] + h * k[j];
+        }
+        rhs(c, ys[3], Fz, eta, k);
+#pragma unroll
+        for (int j = 0; j < 13; ++j) yn[j] = y[j] + (h / 6.0f) * (acc[j] + k[j]);
+    }
+    // normalisation q <- q / |q|
+    float ybn[13];
+#pragma unroll
+    for (int j = 0; j < 13; ++j) ybn[j] = gout[j];
+    {
+        const float nq = sqrtf(yn[6] * yn[6] + yn[7] * yn[7] + yn[8] * yn[8] + yn[9] * yn[9]);
+        const float inv = 1.0f / nq;
+        float d = 0.0f;
+#pragma unroll
+        for (int j = 6; j < 10; ++j) d += yn[j] * inv * gout[j];
+#pragma unroll
+        for (int j = 6; j < 10; ++j) ybn[j] = (gout[j] - yn[j] * inv * d) * inv;
+    }
+    // integrator
+    float yb[13];
+    float Fzb = 0.0f, etab[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int j = 0; j < 13; ++j) yb[j] = ybn[j];
+    if (c.integrator == 1) {
+        float kb[13], t[13];
+#pragma unroll
+        for (int j = 0; j < 13; ++j) {
+            kb[j] = h * ybn[j];
+            t[j] = 0.0f;
+        }
+        rhs_vjp(c, ys[0], Fz, kb, t, Fzb, etab);
+#pragma unroll
+        for (int j = 0; j < 13; ++j) yb[j] += t[j];
+    } else {
+        float kb[13], t[13];
+        // stage 4
+#pragma unroll
+        for (int j = 0; j < 13; ++j) {
+            kb[j] = (h / 6.0f) * ybn[j];
+            t[j] = 0.0f;
+        }
+        rhs_vjp(c, ys[3], Fz, kb, t, Fzb, etab);
+        // stage 3: kb3 = h/3 ybn + h * t4
+#pragma unroll
+        for (int j = 0; j < 13; ++j) {
+            yb[j] += t[j];
+            kb[j] = (h / 3.0f) * ybn[j] + h * t[j];
+            t[j] = 0.0f;
+        }
+        rhs_vjp(c, ys[2], Fz, kb, t, Fzb, etab);
+        // stage 2: kb2 = h/3 ybn + h/2 * t3
+#pragma unroll
+        for (int j = 0; j < 13; ++j) {
+            yb[j] += t[j];
+            kb[j] = (h / 3.0f) * ybn[j] + 0.5f * h * t[j];
+            t[j] = 0.0f;
+        }
+        rhs_vjp(c, ys[1], Fz, kb, t, Fzb, etab);
+        // stage 1: kb1 = h/6 ybn + h/2 * t2
+#pragma unroll
+        for (int j = 0; j < 13; ++j) {
+            yb[j] += t[j];
+            kb[j] = (h / 6.0f) * ybn[j] + 0.5f * h * t[j];
+            t[j] = 0.0f;
+        }
+        rhs_vjp(c, ys[0], Fz, kb, t, Fzb, etab);
+#pragma unroll
+        for (int j = 0; j < 13; ++j) yb[j] += t[j];
+    }
+    // thrust and rotor lag
+    float fb[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float w = y[13 + i];  // lagged rotor speed
+        const float fbi = Fzb + c.mix[0][i] * etab[0] + c.mix[1][i] * etab[1] + c.mix[2][i] * etab[2];
+        const float wb = gout[13 + i] + fbi * (2.0f * c.k2 * w + c.k1);
+        gin[13 + i] = wb * c.decay;
+        const float wdb = tape.in_w[i] ? wb * (1.0f - c.decay) : 0.0f;
+        fb[i] = tape.in_f[i] ? wdb * tape.dw_df[i] : 0.0f;
+    }
+    // controller: f = Ainv * rhs
+    float rb[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) rb[r] = c.Ainv[0][r] * fb[0] + c.Ainv[1][r] * fb[1] + c.Ainv[2][r] * fb[2] + c.Ainv[3][r] * fb[3];
+    gu[0] += rb[0] * c.half_a_max_m;
+    const float* Om = y_in + 10;
+    float L[3] = {c.J[0] * Om[0], c.J[1] * Om[1], c.J[2] * Om[2]};
+    float cb[3] = {rb[1], rb[2], rb[3]};
+    float t1[3], Lb[3];
+    cross3(L, cb, t1);
+    cross3(cb, Om, Lb);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        gu[j + 1] += cb[j] * c.JK[j] * c.rate_max[j];
+        yb[10 + j] += -cb[j] * c.JK[j] + t1[j] + c.J[j] * Lb[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 13; ++j) gin[j] = yb[j];
+}
+
+// Reverse mode of a full control step (n_sub sub-steps): the sub-step start
+// states are recomputed into local memory first.
+__device__ void control_step_vjp(const DynConsts& c, const float y_in[17], const float u[4], const float gout[17],
+                                 float gin[17], float gu[4]) {
+    float g[17];
+#pragma unroll
+    for (int j = 0; j < 17; ++j) g[j] = gout[j];
+    if (c.n_sub == 1) {
+        substep_vjp(c, y_in, u, g, gin, gu);
+        return;
+    }
+    float ys[kMaxSub][17];
+#pragma unroll
+    for (int j = 0; j < 17; ++j) ys[0][j] = y_in[j];
+    for (int s = 1; s < c.n_sub; ++s) {
+#pragma unroll
+        for (int j = 0; j < 17; ++j) ys[s][j] = ys[s - 1][j];
+        substep(c, ys[s], u);
+    }
+    for (int s = c.n_sub - 1; s >= 0; --s) {
+        float gi[17];
+        substep_vjp(c, ys[s], u, g, gi, gu);
+#pragma unroll
+        for (int j = 0; j < 17; ++j) g[j] = gi[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 17; ++j) gin[j] = g[j];
+}
+
+// ---------------------------------------------------------------- kernels
+__device__ __forceinline__ void load_state(const float* __restrict__ s, int n, int a, float y[17]) {
+#pragma unroll
+    for (int j = 0; j < 17; ++j) y[j] = s[(size_t)j * n + a];
+}
+__device__ __forceinline__ void store_state(float* __restrict__ s, int n, int a, const float y[17]) {
+#pragma unroll
+    for (int j = 0; j < 17; ++j) s[(size_t)j * n + a] = y[j];
+}
+__device__ __forceinline__ void load_cmd(const float* __restrict__ u_, int n, int a, float u[4]) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) u[j] = u_[(size_t)j * n + a];
+}
+
+__global__ void __launch_bounds__(128) step_kernel(DynConsts c, int n, float* state, const float* __restrict__ cmd,
+                                                   float* __restrict__ ckpt) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    float y[17], u[4];
+    load_state(state, n, a, y);
+    load_cmd(cmd, n, a, u);
+    if (ckpt) store_state(ckpt, n, a, y);
+    control_step(c, y, u);
+    store_state(state, n, a, y);
+}
+
+__global__ void __launch_bounds__(128) step_backward_kernel(DynConsts c, int n, const float* __restrict__ state_in,
+                                                            const float* __restrict__ cmd,
+                                                            const float* __restrict__ g_out,
+                                                            float* __restrict__ g_in, float* __restrict__ g_cmd) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    float y[17], u[4], go[17], gi[17], gu[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    load_state(state_in, n, a, y);
+    load_cmd(cmd, n, a, u);
+    load_state(g_out, n, a, go);
+    control_step_vjp(c, y, u, go, gi, gu);
+    store_state(g_in, n, a, gi);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) g_cmd[(size_t)j * n + a] = gu[j];
+}
+
+__global__ void __launch_bounds__(128) rollout_kernel(DynConsts c, int n, int T, int K,
+                                                      const float* __restrict__ state0,
+                                                      const float* __restrict__ cmds, float* __restrict__ states_out,
+                                                      float* __restrict__ ckpt, float* __restrict__ state_final) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    float y[17], u[4];
+    load_state(state0, n, a, y);
+    if (states_out) store_state(states_out, n, a, y);
+    for (int t = 0; t < T; ++t) {
+        if (ckpt && t % K == 0) store_state(ckpt + (size_t)(t / K) * 17 * n, n, a, y);
+        load_cmd(cmds + (size_t)t * 4 * n, n, a, u);
+        control_step(c, y, u);
+        if (states_out) store_state(states_out + (size_t)(t + 1) * 17 * n, n, a, y);
+    }
+    if (state_final) store_state(state_final, n, a, y);
+}
+
+// Rollout adjoint with recompute from checkpoints: segment s covers steps
+// [sK, min(sK+K, T)); its states are re-run from ckpt[s] into local memory and
+// swept backwards.  g_states[t] is added to the running cotangent of state t.
+__global__ void __launch_bounds__(64) rollout_backward_kernel(DynConsts c, int n, int T, int K,
+                                                              const float* __restrict__ ckpt,
+                                                              const float* __restrict__ cmds,
+                                                              const float* __restrict__ g_states,
+                                                              float* __restrict__ g_state0,
+                                                              float* __restrict__ g_cmds) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    float seg[kMaxCkptK][17];
+    float g[17];
+    load_state(g_states + (size_t)T * 17 * n, n, a, g);
+    const int nseg = (T + K - 1) / K;
+    for (int s = nseg - 1; s >= 0; --s) {
+        const int t0 = s * K;
+        const int t1 = min(t0 + K, T);
+        load_state(ckpt + (size_t)s * 17 * n, n, a, seg[0]);
+        for (int t = t0 + 1; t < t1; ++t) {
+            float u[4];
+#pragma unroll
+            for (int j = 0; j < 17; ++j) seg[t - t0][j] = seg[t - t0 - 1][j];
+            load_cmd(cmds + (size_t)(t - 1) * 4 * n, n, a, u);
+            control_step(c, seg[t - t0], u);
+        }
+        for (int t = t1 - 1; t >= t0; --t) {
+            float u[4], gi[17], gu[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            load_cmd(cmds + (size_t)t * 4 * n, n, a, u);
+            control_step_vjp(c, seg[t - t0], u, g, gi, gu);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) g_cmds[((size_t)t * 4 + j) * n + a] = gu[j];
+            float gs[17];
+            load_state(g_states + (size_t)t * 17 * n, n, a, gs);
+#pragma unroll
+            for (int j = 0; j < 17; ++j) g[j] = gi[j] + gs[j];
+        }
+    }
+    store_state(g_state0, n, a, g);
+}
+
+inline unsigned blocks_for(int n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+cudaError_t launch_step(const DynConsts& c, int n, float* state, const float* cmd, float* ckpt, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    step_kernel<<<blocks_for(n, 128), 128, 0, s>>>(c, n, state, cmd, ckpt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_backward(const DynConsts& c, int n, const float* state_in, const float* cmd,
+                                 const float* g_out, float* g_in, float* g_cmd, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    step_backward_kernel<<<blocks_for(n, 128), 128, 0, s>>>(c, n, state_in, cmd, g_out, g_in, g_cmd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rollout(const DynConsts& c, int n, int T, int K, const float* state0, const float* cmds,
+                           float* states_out, float* ckpt, float* state_final, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    rollout_kernel<<<blocks_for(n, 128), 128, 0, s>>>(c, n, T, K, state0, cmds, states_out, ckpt, state_final);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rollout_backward(const DynConsts& c, int n, int T, int K, const float* ckpt, const float* cmds,
+                                    const float* g_states, float* g_state0, float* g_cmds, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    rollout_backward_kernel<<<blocks_for(n, 64), 64, 0, s>>>(c, n, T, K, ckpt, cmds, g_states, g_state0, g_cmds);
+    return cudaGetLastError();
+}
+
+}  // namespace vf

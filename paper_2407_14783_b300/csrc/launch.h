@@ -1,0 +1,59 @@
+// Host-side launch interfaces between the C ABI and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace vf {
+
+// dynamics.cu
+cudaError_t launch_step(const DynConsts& c, int n, float* state, const float* cmd, float* ckpt, cudaStream_t s);
+cudaError_t launch_step_backward(const DynConsts& c, int n, const float* state_in, const float* cmd,
+                                 const float* g_out, float* g_in, float* g_cmd, cudaStream_t s);
+cudaError_t launch_rollout(const DynConsts& c, int n, int T, int K, const float* state0, const float* cmds,
+                           float* states_out, float* ckpt, float* state_final, cudaStream_t s);
+cudaError_t launch_rollout_backward(const DynConsts& c, int n, int T, int K, const float* ckpt, const float* cmds,
+                                    const float* g_states, float* g_state0, float* g_cmds, cudaStream_t s);
+
+// lbvh.cu
+struct LbvhResult {
+    float lo[3], hi[3];
+    int n_large, n_bvh, n_nodes, depth, root;
+    float4* nodes;
+    float4* tris;
+    float4* large;
+    uint32_t* colors;
+};
+// Called once the counts are known; must allocate nodes (4 float4 each), tris
+// (3 float4 each, n_bvh), large (3 float4 each, n_large), colors (n_tris).
+typedef cudaError_t (*LbvhAlloc)(void* user, LbvhResult* r);
+size_t lbvh_scratch_bytes(int64_t nt);
+cudaError_t lbvh_build(int64_t nt, const float* d_verts, const int* d_tris, const uint8_t* d_rgb, void* scratch,
+                       LbvhAlloc alloc, void* alloc_user, LbvhResult* out, cudaStream_t s);
+
+// raycast.cu
+struct RenderArgs {
+    int n_agents;
+    const int* scene_of_agent;
+    const float* state;
+    float* depth;
+    uint8_t* rgb;
+    int* hit_id;
+    const SceneRow* table;
+    int n_scenes;
+    CamConsts cam;
+    unsigned* counter;   // work-item counter (zero between launches)
+    unsigned* done;      // finished-CTA counter (zero between launches)
+    int* err;
+    long long* counters; // traversal counters (COUNT builds)
+};
+size_t render_smem_bytes(int warps_per_cta, int stack_depth, int rpl);
+int render_config_list(sim_render_config* out, int max);
+bool render_config_valid(const sim_render_config& c);
+cudaError_t launch_render(const RenderArgs& a, const sim_render_config& c, int ctas, bool count, cudaStream_t s);
+// api.cu: launches a raycast kernel instance with the persistent grid size.
+cudaError_t launch_cfg(const void* kernel, const RenderArgs& a, int warps_per_cta, int ctas, size_t smem,
+                       cudaStream_t s);
+
+}  // namespace vf

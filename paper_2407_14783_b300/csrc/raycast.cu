@@ -1,0 +1,370 @@
+// Persistent ray-cast renderer: 64x64 FP32 depth + uint8 RGB per agent
+// (the depth and colour sensors of Sec. III-B), sm_103a.
+//
+// One warp renders one image tile of 32 * RPL pixels (one or two rays per
+// lane) and pulls the next (agent, tile) item from a global counter, so scenes
+// of very different size load-balance inside one launch.  The warp walks its
+// agent's scene BVH as a packet: a node's 64 bytes are fetched by four lanes
+// with coalesced float4 loads into the warp's shared-memory slot and read back
+// by every lane; each lane slab-tests both child boxes against its own rays and
+// a warp vote (__ballot_sync) decides which children any ray needs, near child
+// first, the other pushed on the warp's stack (shared memory or a stack spread
+// over the lanes' registers).  Leaves (up to 4 triangles, 12 float4, contiguous
+// in leaf order) are staged the same way and every lane runs Moller-Trumbore on
+// them.  The walk ends when the stack is empty; the votes skip every subtree
+// that no lane of the tile can reach before its current closest hit.
+//
+// Result per ray: the closest hit with max_depth >= t > 1e-6 and, among equal
+// FP32 t, the lowest triangle id (order-independent, so every configuration
+// gives identical images).  Stores are packed: depth as one float per lane,
+// colour bytes gathered in shared memory and written as 32-bit words.
+#include "common.cuh"
+#include "launch.h"
+
+namespace vf {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kTmin = 1e-6f;
+constexpr int kIterCap = 1 << 18;  // node + leaf visits per work item
+
+struct Ray {
+    float o[3], d[3], inv[3], ood[3];
+    float best_t;
+    int best_id;
+    bool live;
+};
+
+__device__ __forceinline__ void mt_test(Ray& r, const float4 a, const float4 b, const float4 c) {
+    // a = (v0, id), b = e1, c = e2; two-sided Moller-Trumbore
+    const float px = r.d[1] * c.z - r.d[2] * c.y;
+    const float py = r.d[2] * c.x - r.d[0] * c.z;
+    const float pz = r.d[0] * c.y - r.d[1] * c.x;
+    const float det = b.x * px + b.y * py + b.z * pz;
+    const float inv = 1.0f / det;
+    const float sx = r.o[0] - a.x, sy = r.o[1] - a.y, sz = r.o[2] - a.z;
+    const float u = (sx * px + sy * py + sz * pz) * inv;
+    const float qx = sy * b.z - sz * b.y;
+    const float qy = sz * b.x - sx * b.z;
+    const float qz = sx * b.y - sy * b.x;
+    const float v = (r.d[0] * qx + r.d[1] * qy + r.d[2] * qz) * inv;
+    const float t = (c.x * qx + c.y * qy + c.z * qz) * inv;
+    const int id = __float_as_int(a.w);
+    const bool hit = det != 0.0f && u >= 0.0f && v >= 0.0f && u + v <= 1.0f && t > kTmin &&
+                     (t < r.best_t || (t == r.best_t && (unsigned)id < (unsigned)r.best_id));
+    if (hit && r.live) {
+        r.best_t = t;
+        r.best_id = id;
+    }
+}
+
+// Slab test of one child box against a ray; entry distance in tn.
+__device__ __forceinline__ bool slab(const Ray& r, float lx, float ly, float lz, float hx, float hy, float hz,
+                                     float& tn) {
+    const float x0 = fmaf(lx, r.inv[0], -r.ood[0]), x1 = fmaf(hx, r.inv[0], -r.ood[0]);
+    const float y0 = fmaf(ly, r.inv[1], -r.ood[1]), y1 = fmaf(hy, r.inv[1], -r.ood[1]);
+    const float z0 = fmaf(lz, r.inv[2], -r.ood[2]), z1 = fmaf(hz, r.inv[2], -r.ood[2]);
+    tn = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), 0.0f));
+    const float tf = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), r.best_t));
+    return r.live && tn <= tf;
+}
+
+template <int RPL>
+__device__ __forceinline__ void test_tris_staged(Ray (&ray)[RPL], const float4* __restrict__ src, int count,
+                                                 float4* stage, int lane) {
+    // count <= kLeafMax: lanes 0 .. 3*count-1 fetch one float4 each (contiguous)
+    __syncwarp();
+    if (lane < 3 * count) stage[lane] = __ldg(src + lane);
+    __syncwarp();
+    for (int k = 0; k < count; ++k) {
+        const float4 a = stage[3 * k], b = stage[3 * k + 1], c = stage[3 * k + 2];
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) mt_test(ray[q], a, b, c);
+    }
+}
+
+template <int TW, int TH, int RPL, bool SMEM_STACK, int STACK, bool COUNT>
+__global__ void __launch_bounds__(256) raycast_kernel(RenderArgs A) {
+    static_assert(TW * TH == 32 * RPL, "tile must hold 32 * RPL pixels");
+    extern __shared__ float4 smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wpc = blockDim.x >> 5;
+    float4* stage = smem + warp * 12;
+    int* sstack = reinterpret_cast<int*>(smem + wpc * 12) + warp * STACK;
+    uint8_t* rgbstage = reinterpret_cast<uint8_t*>(reinterpret_cast<int*>(smem + wpc * 12) + wpc * STACK) +
+                        warp * (32 * RPL * 3);
+
+    const int W = A.cam.W, H = A.cam.H;
+    const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
+    const int tiles = tiles_x * tiles_y;
+    const long long total = (long long)A.n_agents * tiles;
+    long long n_nodes = 0, n_tris = 0, n_large = 0, n_items = 0;
+
+    for (;;) {
+        long long item = 0;
+        if (lane == 0) item = (long long)atomicAdd(A.counter, 1u);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= total) break;
+        // after a device-detected fault every warp stops taking work
+        if (__shfl_sync(kFull, lane == 0 ? *(volatile int*)A.err : 0, 0) == kDevErrTraversal) break;
+        const int agent = (int)(item / tiles);
+        const int tile = (int)(item - (long long)agent * tiles);
+        const int tx0 = (tile % tiles_x) * TW, ty0 = (tile / tiles_x) * TH;
+        const int sid = __ldg(A.scene_of_agent + agent);
+        const bool scene_ok = sid >= 0 && sid < A.n_scenes && A.table[sid].live;
+        if (!scene_ok && lane == 0) set_error(A.err, kDevErrNotFound);
+        SceneRow row;
+        if (scene_ok) row = A.table[sid];
+
+        // camera pose of this agent (uniform loads)
+        const float* st = A.state;
+        const int n = A.n_agents;
+        const float px = __ldg(st + agent), py = __ldg(st + n + agent), pz = __ldg(st + 2 * n + agent);
+        const float qw = __ldg(st + 6 * n + agent), qx = __ldg(st + 7 * n + agent), qy = __ldg(st + 8 * n + agent),
+                    qz = __ldg(st + 9 * n + agent);
+        const float inv_n = 1.0f / (qw * qw + qx * qx + qy * qy + qz * qz);
+        float R[3][3];
+        R[0][0] = (qw * qw + qx * qx - qy * qy - qz * qz) * inv_n;
+        R[0][1] = 2.0f * (qx * qy - qw * qz) * inv_n;
+        R[0][2] = 2.0f * (qx * qz + qw * qy) * inv_n;
+        R[1][0] = 2.0f * (qx * qy + qw * qz) * inv_n;
+        R[1][1] = (qw * qw - qx * qx + qy * qy - qz * qz) * inv_n;
+        R[1][2] = 2.0f * (qy * qz - qw * qx) * inv_n;
+        R[2][0] = 2.0f * (qx * qz - qw * qy) * inv_n;
+        R[2][1] = 2.0f * (qy * qz + qw * qx) * inv_n;
+        R[2][2] = (qw * qw - qx * qx - qy * qy + qz * qz) * inv_n;
+        const float ox = px + R[0][0] * A.cam.cam_off[0] + R[0][1] * A.cam.cam_off[1] + R[0][2] * A.cam.cam_off[2];
+        const float oy = py + R[1][0] * A.cam.cam_off[0] + R[1][1] * A.cam.cam_off[1] + R[1][2] * A.cam.cam_off[2];
+        const float oz = pz + R[2][0] * A.cam.cam_off[0] + R[2][1] * A.cam.cam_off[1] + R[2][2] * A.cam.cam_off[2];
+
+        Ray ray[RPL];
+        int pix_r[RPL], pix_c[RPL];
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const int p = lane + 32 * q;
+            const int c = tx0 + p % TW, r = ty0 + p / TW;
+            pix_r[q] = r;
+            pix_c[q] = c;
+            const float dy = -(float)(2 * c + 1 - W) * 0.5f * A.cam.pix;
+            const float dz = -(float)(2 * r + 1 - H) * 0.5f * A.cam.pix;
+            const float dB[3] = {1.0f, dy, dz};
+            Ray& ry = ray[q];
+            ry.o[0] = ox; ry.o[1] = oy; ry.o[2] = oz;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                ry.d[j] = R[j][0] * dB[0] + R[j][1] * dB[1] + R[j][2] * dB[2];
+                ry.inv[j] = 1.0f / ry.d[j];
+                ry.ood[j] = ry.o[j] * ry.inv[j];
+            }
+            ry.best_t = A.cam.max_depth;
+            ry.best_id = -1;
+            ry.live = scene_ok && r < H && c < W;
+        }
+
+        if (scene_ok) {
+            // large triangles: every ray tests them
+            for (int k0 = 0; k0 < row.n_large; k0 += kLeafMax) {
+                const int cnt = min(kLeafMax, row.n_large - k0);
+                test_tris_staged<RPL>(ray, row.large + 3 * k0, cnt, stage, lane);
+                if (COUNT) n_large += cnt;
+            }
+            // BVH walk
+            int cur = row.root;
+            int sp = 0;
+            int reg0 = 0, reg1 = 0;  // register stack: entry k in lane k % 32 of reg[k / 32]
+            int iters = 0;
+            while (cur != kEmptyRoot) {
+                if (++iters > kIterCap) {
+                    if (lane == 0) set_error(A.err, kDevErrTraversal);
+                    break;
+                }
+                int next = kEmptyRoot;
+                if (cur >= 0) {
+                    const float4* np = row.nodes + 4 * (size_t)cur;
+                    __syncwarp();
+                    if (lane < 4) stage[lane] = __ldg(np + lane);
+                    __syncwarp();
+                    const float4 n0 = stage[0], n1 = stage[1], n2 = stage[2], n3 = stage[3];
+                    if (COUNT) ++n_nodes;
+                    bool h0 = false, h1 = false, pref1 = false;
+#pragma unroll
+                    for (int q = 0; q < RPL; ++q) {
+                        float t0, t1;
+                        const bool a = slab(ray[q], n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, t0);
+                        const bool b = slab(ray[q], n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, t1);
+                        h0 |= a;
+                        h1 |= b;
+                        pref1 |= a && b && t1 < t0;
+                    }
+                    const unsigned b0 = __ballot_sync(kFull, h0), b1 = __ballot_sync(kFull, h1);
+                    const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+                    if (b0 && b1) {
+                        const unsigned both = b0 & b1;
+                        const bool near1 = 2 * __popc(__ballot_sync(kFull, pref1)) > __popc(both);
+                        const int far = near1 ? c0 : c1;
+                        next = near1 ? c1 : c0;
+                        if (sp >= STACK) {
+                            if (lane == 0) set_error(A.err, kDevErrTraversal);
+                            break;
+                        }
+                        if (SMEM_STACK) {
+                            if (lane == 0) sstack[sp] = far;
+                        } else {
+                            if (lane == (sp & 31)) {
+                                if (sp < 32) reg0 = far; else reg1 = far;
+                            }
+                        }
+                        ++sp;
+                    } else if (b0) {
+                        next = c0;
+                    } else if (b1) {
+                        next = c1;
+                    }
+                } else {
+                    int first, count;
+                    leaf_decode(cur, first, count);
+                    test_tris_staged<RPL>(ray, row.tris + 3 * (size_t)first, count, stage, lane);
+                    if (COUNT) n_tris += count;
+                }
+                if (next == kEmptyRoot) {
+                    if (sp == 0) break;
+                    --sp;
+                    if (SMEM_STACK) {
+                        __syncwarp();
+                        next = sstack[sp];
+                    } else {
+                        next = __shfl_sync(kFull, sp < 32 ? reg0 : reg1, sp & 31);
+                    }
+                }
+                cur = next;
+            }
+        }
+
+        // stores
+        const size_t frame = (size_t)agent * H * W;
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const bool in = pix_r[q] < H && pix_c[q] < W;
+            const size_t off = frame + (size_t)pix_r[q] * W + pix_c[q];
+            if (in && A.depth) A.depth[off] = ray[q].best_t;
+            if (in && A.hit_id) A.hit_id[off] = ray[q].best_id;
+            if (A.rgb) {
+                const uint32_t col = ray[q].best_id >= 0 ? __ldg(row.colors + ray[q].best_id) : 0u;
+                const int p = lane + 32 * q;
+                rgbstage[3 * p + 0] = (uint8_t)(col & 0xFF);
+                rgbstage[3 * p + 1] = (uint8_t)((col >> 8) & 0xFF);
+                rgbstage[3 * p + 2] = (uint8_t)((col >> 16) & 0xFF);
+            }
+        }
+        if (A.rgb) {
+            __syncwarp();
+            if ((W % 4) == 0 && (TW % 4) == 0 && tx0 + TW <= W && ty0 + TH <= H &&
+                (reinterpret_cast<uintptr_t>(A.rgb) & 3) == 0) {
+                // each tile row is TW*3 bytes starting at a 4-byte-aligned offset
+                constexpr int words_per_row = TW * 3 / 4;
+                constexpr int words = words_per_row * TH;
+                for (int w = lane; w < words; w += 32) {
+                    const int r = w / words_per_row, k = w % words_per_row;
+                    const uint32_t* srcw = reinterpret_cast<const uint32_t*>(rgbstage + r * TW * 3) + k;
+                    uint32_t* dstw = reinterpret_cast<uint32_t*>(A.rgb + 3 * (frame + (size_t)(ty0 + r) * W + tx0)) + k;
+                    *dstw = *srcw;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) {
+                    if (pix_r[q] < H && pix_c[q] < W) {
+                        const int p = lane + 32 * q;
+                        uint8_t* dst = A.rgb + 3 * (frame + (size_t)pix_r[q] * W + pix_c[q]);
+                        dst[0] = rgbstage[3 * p];
+                        dst[1] = rgbstage[3 * p + 1];
+                        dst[2] = rgbstage[3 * p + 2];
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        if (COUNT) ++n_items;
+    }
+
+    if (COUNT && lane == 0) {
+        atomicAdd((unsigned long long*)&A.counters[0], (unsigned long long)n_nodes);
+        atomicAdd((unsigned long long*)&A.counters[1], (unsigned long long)n_tris);
+        atomicAdd((unsigned long long*)&A.counters[2], (unsigned long long)n_large);
+        atomicAdd((unsigned long long*)&A.counters[3], (unsigned long long)n_items);
+    }
+    // the last CTA to finish resets the work counter for the next launch
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(A.done, 1u) == gridDim.x - 1) {
+            *A.counter = 0u;
+            *A.done = 0u;
+            __threadfence();
+        }
+    }
+}
+
+template <int TW, int TH, int RPL, bool SMEM_STACK, int STACK, bool COUNT>
+cudaError_t launch_one(const RenderArgs& a, int warps_per_cta, int ctas, cudaStream_t s) {
+    auto k = raycast_kernel<TW, TH, RPL, SMEM_STACK, STACK, COUNT>;
+    const size_t shm = render_smem_bytes(warps_per_cta, STACK, RPL);
+    return launch_cfg(reinterpret_cast<const void*>(k), a, warps_per_cta, ctas, shm, s);
+}
+
+template <bool COUNT>
+cudaError_t dispatch(const RenderArgs& a, const sim_render_config& c, int ctas, cudaStream_t s) {
+#define VF_CASE(TW, TH, RPL)                                                                                   \
+    if (c.tile_w == TW && c.tile_h == TH && c.rays_per_lane == RPL) {                                         \
+        if (c.stack_in_smem) {                                                                                 \
+            if (c.stack_depth <= 32) return launch_one<TW, TH, RPL, true, 32, COUNT>(a, c.warps_per_cta, ctas, s); \
+            return launch_one<TW, TH, RPL, true, 64, COUNT>(a, c.warps_per_cta, ctas, s);                     \
+        }                                                                                                      \
+        if (c.stack_depth <= 32) return launch_one<TW, TH, RPL, false, 32, COUNT>(a, c.warps_per_cta, ctas, s); \
+        return launch_one<TW, TH, RPL, false, 64, COUNT>(a, c.warps_per_cta, ctas, s);                        \
+    }
+    VF_CASE(8, 4, 1)
+    VF_CASE(4, 8, 1)
+    VF_CASE(16, 2, 1)
+    VF_CASE(8, 8, 2)
+    VF_CASE(16, 4, 2)
+#undef VF_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+size_t render_smem_bytes(int warps_per_cta, int stack_depth, int rpl) {
+    const int st = stack_depth <= 32 ? 32 : 64;
+    return (size_t)warps_per_cta * (12 * sizeof(float4) + st * sizeof(int) + 32 * rpl * 3);
+}
+
+int render_config_list(sim_render_config* out, int max) {
+    static const int shapes[][3] = {{8, 4, 1}, {4, 8, 1}, {16, 2, 1}, {8, 8, 2}, {16, 4, 2}};
+    int k = 0;
+    for (const auto& sh : shapes)
+        for (int smem = 0; smem <= 1; ++smem)
+            for (int wpc : {4, 8}) {
+                if (k < max && out) out[k] = sim_render_config{sh[0], sh[1], sh[2], smem, 64, wpc, 0};
+                ++k;
+            }
+    return k;
+}
+
+bool render_config_valid(const sim_render_config& c) {
+    sim_render_config all[64];
+    const int n = render_config_list(all, 64);
+    for (int i = 0; i < n; ++i) {
+        const sim_render_config& a = all[i];
+        if (a.tile_w == c.tile_w && a.tile_h == c.tile_h && a.rays_per_lane == c.rays_per_lane &&
+            (c.warps_per_cta == 2 || c.warps_per_cta == 4 || c.warps_per_cta == 8) &&
+            (c.stack_depth == 32 || c.stack_depth == 64) && c.ctas_per_sm >= 0 && c.ctas_per_sm <= 32)
+            return true;
+    }
+    return false;
+}
+
+cudaError_t launch_render(const RenderArgs& a, const sim_render_config& c, int ctas, bool count, cudaStream_t s) {
+    return count ? dispatch<true>(a, c, ctas, s) : dispatch<false>(a, c, ctas, s);
+}
+
+}  // namespace vf

@@ -33,3 +33,26 @@ def gpu_available():
         return torch.cuda.is_available()
     except Exception:
         return False
+
+
+@pytest.fixture(scope="session")
+def cuda_lib():
+    """The built CUDA library; GPU tests fail loudly (no fallback) if it is missing."""
+    from paper_2407_14783_b300 import build, binding
+    build.build()
+    return binding.lib()
+
+
+@pytest.fixture
+def make_sim(cuda_lib):
+    from paper_2407_14783_b300.sim import Sim
+    made = []
+
+    def _make(params, **kw):
+        s = Sim(params, **kw)
+        made.append(s)
+        return s
+
+    yield _make
+    for s in made:
+        s.close()

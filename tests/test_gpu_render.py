@@ -1,0 +1,142 @@
+"""GPU LBVH build + persistent ray cast against the FP64 oracle (Sec. III-B)."""
+import numpy as np
+import pytest
+import torch
+
+from parity import compare_images
+
+pytestmark = pytest.mark.gpu
+
+
+def _render(sim, sid_or_ids, s32):
+    from paper_2407_14783_b300.sim import to_soa
+    n = s32.shape[0]
+    st = to_soa(s32)
+    ids = sid_or_ids if isinstance(sid_or_ids, torch.Tensor) else torch.full((n,), sid_or_ids, dtype=torch.int32,
+                                                                             device="cuda")
+    d, c, h = sim.alloc_images(n, hit=True)
+    sim.render(ids, st, d, c, h)
+    torch.cuda.synchronize()
+    sim.check()
+    return d.cpu().numpy(), c.cpu().numpy(), h.cpu().numpy()
+
+
+def test_render_parity_tiny(make_sim, oracle_mod, wl):
+    """492-triangle room, 4 agents (the tiny configuration)."""
+    p = wl.params()
+    sc = wl.room_scene()
+    sim = make_sim(p)
+    sid = sim.add_workload_scene(sc)
+    s = wl.spawn_states(sc, 4, 3, 1100.0).astype(np.float32)
+    d, c, h = _render(sim, sid, s)
+    stats = compare_images(oracle_mod.Scene.from_workload(sc), p, s.astype(np.float64), d, c, h)
+    assert stats["hit_frac"] > 0.9
+
+
+def test_render_parity_large_scene_sampled(make_sim, oracle_mod, wl):
+    """208,812-triangle cluttered room at the benchmark's launch shape (256 agents,
+    one launch); the oracle checks 24 sampled agents' full images."""
+    p = wl.params()
+    sc = wl.cluttered_scene()
+    sim = make_sim(p)
+    sid = sim.add_workload_scene(sc)
+    info = sim.scene_info(sid)
+    assert info["n_tris"] == sc.n_tris and info["n_large"] == 12
+    s = wl.spawn_states(sc, 256, 3, 1100.0).astype(np.float32)
+    d, c, h = _render(sim, sid, s)
+    pick = np.random.default_rng(0).choice(256, 24, replace=False)
+    compare_images(oracle_mod.Scene.from_workload(sc), p, s[pick].astype(np.float64), d[pick], c[pick], h[pick])
+
+
+def test_render_configs_identical(make_sim, wl):
+    """Every supported tile shape / rays-per-lane / stack placement gives the same
+    images (the closest-hit rule with lowest-id ties is order independent)."""
+    from paper_2407_14783_b300.sim import Sim
+    p = wl.params()
+    sc = wl.cluttered_scene(n_objects=400, size=(20.0, 20.0, 6.0), seed=4)
+    sim = make_sim(p)
+    sid = sim.add_workload_scene(sc)
+    s = wl.spawn_states(sc, 37, 5, 1100.0).astype(np.float32)
+    base = None
+    for cfg in Sim.render_configs():
+        sim.set_render_config(cfg)
+        out = _render(sim, sid, s)
+        if base is None:
+            base = out
+        else:
+            for a, b in zip(out, base):
+                assert np.array_equal(a, b), cfg
+
+
+@pytest.mark.parametrize("wh", [(30, 18), (64, 64), (128, 96), (7, 5)])
+def test_render_ragged_image_sizes(make_sim, oracle_mod, wl, wh):
+    """Image sizes that leave partial tiles."""
+    p = wl.params(width=wh[0], height=wh[1])
+    sc = wl.room_scene()
+    sim = make_sim(p)
+    sid = sim.add_workload_scene(sc)
+    s = wl.spawn_states(sc, 5, 6, 1100.0).astype(np.float32)
+    d, c, h = _render(sim, sid, s)
+    compare_images(oracle_mod.Scene.from_workload(sc), p, s.astype(np.float64), d, c, h, max_tie_frac=0.02)
+
+
+def test_multi_scene_one_launch_equals_per_scene(make_sim, oracle_mod, wl):
+    """Scenes of uneven size in one launch through the scene table give the same
+    images as rendering each scene's agents alone, and match the oracle."""
+    p = wl.params()
+    scenes = [wl.room_scene(seed=1), wl.cluttered_scene(n_objects=50, size=(10.0, 10.0, 4.0), seed=2),
+              wl.cluttered_scene(n_objects=600, size=(25.0, 25.0, 6.0), seed=3)]
+    sim = make_sim(p)
+    sids = [sim.add_workload_scene(s) for s in scenes]
+    counts = [3, 9, 20]
+    states = [wl.spawn_states(s, k, 10 + i, 1100.0).astype(np.float32) for i, (s, k) in enumerate(zip(scenes, counts))]
+    all_s = np.concatenate(states)
+    ids = torch.tensor(np.repeat(sids, counts), dtype=torch.int32, device="cuda")
+    d, c, h = _render(sim, ids, all_s)
+    off = 0
+    for sc, sid, st, k in zip(scenes, sids, states, counts):
+        d1, c1, h1 = _render(sim, sid, st)
+        assert np.array_equal(d[off:off + k], d1) and np.array_equal(c[off:off + k], c1)
+        assert np.array_equal(h[off:off + k], h1)
+        compare_images(oracle_mod.Scene.from_workload(sc), p, st.astype(np.float64), d1, c1, h1)
+        off += k
+
+
+def test_degenerate_scenes(make_sim, oracle_mod, wl):
+    """Empty scene (all misses), a single triangle, and a scene of only large
+    triangles (no BVH)."""
+    p = wl.params()
+    sim = make_sim(p)
+    s = np.zeros((2, 17), np.float32)
+    s[:, 6] = 1.0
+    s[1, 0:3] = [0.5, 0.2, -0.1]
+    e = sim.add_scene(np.zeros((0, 3)), np.zeros((0, 3)), np.zeros((0, 3)))
+    d, c, h = _render(sim, e, s)
+    assert np.all(h == -1) and np.all(d == p["max_depth"]) and np.all(c == 0)
+    v = np.array([[3.0, -1.0, -1.0], [3.0, 1.5, -1.0], [3.0, 0.0, 2.0]])
+    one = sim.add_scene(v, [[0, 1, 2]], [[10, 20, 30]])
+    d, c, h = _render(sim, one, s)
+    compare_images(oracle_mod.Scene(v, [[0, 1, 2]], [[10, 20, 30]]), p, s.astype(np.float64), d, c, h,
+                   max_tie_frac=0.05)
+    bv, bf = wl.box_mesh((-5, -5, -3), (5, 5, 3))
+    rgb = np.arange(36, dtype=np.uint8).reshape(12, 3)
+    big = sim.add_scene(bv, bf, rgb)
+    assert sim.scene_info(big)["n_large"] == 12
+    d, c, h = _render(sim, big, s)
+    compare_images(oracle_mod.Scene(bv, bf, rgb), p, s.astype(np.float64), d, c, h, max_tie_frac=0.05)
+
+
+def test_unknown_scene_is_reported(make_sim, wl):
+    p = wl.params()
+    sim = make_sim(p)
+    sid = sim.add_workload_scene(wl.room_scene())
+    s = np.zeros((3, 17), np.float32)
+    s[:, 6] = 1.0
+    s[:, 0:3] = (5.0, 5.0, 2.0)     # inside the 10 x 10 x 4 m room
+    ids = torch.tensor([sid, 7, sid], dtype=torch.int32, device="cuda")
+    from paper_2407_14783_b300.sim import to_soa
+    d, c, h = sim.alloc_images(3, hit=True)
+    sim.render(ids, to_soa(s), d, c, h)
+    assert sim.status() == -4          # SIM_ERR_NOT_FOUND, read and cleared
+    assert sim.status() == 0
+    assert torch.all(h[1] == -1) and torch.all(h[0] >= 0)
