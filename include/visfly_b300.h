@@ -141,6 +141,26 @@ int sim_render(sim_ctx* ctx, int32_t n_agents, const int32_t* scene_of_agent, co
 int sim_render_scene(sim_ctx* ctx, int32_t n_agents, int32_t scene_id, const float* state, float* depth,
                      uint8_t* rgb, int32_t* hit_id, void* stream);
 
+/* As sim_render_scene, but allocates no device memory (no cudaMalloc, no
+ * cudaFree, no allocating library call).  The paper has no counterpart: this
+ * is for callers that cannot allocate device memory while they run -- a control
+ * loop that must not touch the allocator after set-up, or a process whose
+ * device memory is handed in full to another framework's pool -- whereas
+ * sim_render_scene allocates its agent -> scene id array on every call.
+ * Scratch (that id array and the ray-cast kernel's two work counters) lives in
+ * one file-scope device array of 256 B + 4 B * SIM_RENDER_STATIC_MAX_AGENTS
+ * (256.25 KiB) that every GPU which loads the library holds until the process
+ * exits.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the context's device current; make that first
+ * call before any stream capture.  Every call shares the one array and clears
+ * its counters before rendering, so calls whose work overlaps on the GPU (other
+ * streams, other contexts on the same device) race: serialise them.
+ * Errors: INVALID_ARG when n_agents > SIM_RENDER_STATIC_MAX_AGENTS or < 0,
+ * NOT_FOUND for an unknown scene, CUDA for a launch failure. */
+#define SIM_RENDER_STATIC_MAX_AGENTS 65536
+int sim_render_scene_static(sim_ctx* ctx, int32_t n_agents, int32_t scene_id, const float* state, float* depth,
+                            uint8_t* rgb, int32_t* hit_id, void* stream);
+
 /* Reverse-mode derivative of one sim_step (the dynamics are differentiable,
  * Sec. III-A): given the pre-step state, the command and the cotangent of the
  * post-step state, write the cotangents of the pre-step state and the command.

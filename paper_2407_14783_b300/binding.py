@@ -83,6 +83,7 @@ SIGNATURES = {
     "sim_step": [_vp, _i32, _vp, _vp, _vp, _vp],
     "sim_render": [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
     "sim_render_scene": [_vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp],
+    "sim_render_scene_static": [_vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp],
     "sim_step_backward": [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
     "sim_rollout": [_vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
     "sim_rollout_backward": [_vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp],

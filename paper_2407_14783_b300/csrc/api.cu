@@ -804,3 +804,31 @@ extern "C" int sim_probe_read_bandwidth(sim_ctx* c, size_t bytes, int32_t iters,
     *gbs = (double)n4 * 16.0 * iters / (ms * 1e-3) / 1e9;
     return SIM_OK;
 }
+
+namespace vf {
+
+void set_last_error(const char* msg) { g_err = msg; }
+
+int ctx_device(const sim_ctx* c) { return c ? c->device : -1; }
+
+// Render n agents of one scene with caller-supplied scratch: soa_dev holds the
+// scene id of every agent and counters_dev the two work counters, already
+// zero.  Same checks and kernel as sim_render.
+int render_scene_with_scratch(sim_ctx* c, int n, int scene_id, const int32_t* soa_dev, unsigned* counters_dev,
+                              const float* state, float* depth, uint8_t* rgb, int32_t* hit, cudaStream_t s) {
+    if (!c) return fail(SIM_ERR_INVALID_ARG, "null context");
+    if (scene_id < 0 || scene_id >= (int)c->scenes.size() || !c->scenes[scene_id].live)
+        return fail(SIM_ERR_NOT_FOUND, "no such scene");
+    int rc = check_render_args(c, n, soa_dev, state);
+    if (rc) return rc;
+    if (n == 0) return SIM_OK;
+    DeviceGuard g(c->device);
+    RenderArgs a = render_args(c, n, soa_dev, state, depth, rgb, hit);
+    a.counter = counters_dev;
+    a.done = counters_dev + 1;
+    int ctas = c->rcfg.ctas_per_sm > 0 ? c->rcfg.ctas_per_sm * c->num_sms : 0;
+    cudaError_t e = launch_render(a, c->rcfg, ctas, false, s);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e, "ray-cast launch");
+}
+
+}  // namespace vf

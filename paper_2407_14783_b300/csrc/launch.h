@@ -52,6 +52,11 @@ size_t render_smem_bytes(int warps_per_cta, int stack_depth, int rpl);
 int render_config_list(sim_render_config* out, int max);
 bool render_config_valid(const sim_render_config& c);
 cudaError_t launch_render(const RenderArgs& a, const sim_render_config& c, int ctas, bool count, cudaStream_t s);
+// api.cu: context helpers for entry points defined in other files.
+void set_last_error(const char* msg);
+int ctx_device(const sim_ctx* c);
+int render_scene_with_scratch(sim_ctx* c, int n, int scene_id, const int32_t* soa_dev, unsigned* counters_dev,
+                              const float* state, float* depth, uint8_t* rgb, int32_t* hit, cudaStream_t s);
 // api.cu: launches a raycast kernel instance with the persistent grid size.
 cudaError_t launch_cfg(const void* kernel, const RenderArgs& a, int warps_per_cta, int ctas, size_t smem,
                        cudaStream_t s);
