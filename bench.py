@@ -22,7 +22,6 @@ import os
 import statistics
 import subprocess
 import sys
-import threading
 import time
 
 import numpy as np
@@ -52,7 +51,8 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 20 ms during the
+    timed region (one nvidia-smi process in loop mode)."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -61,38 +61,41 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.rows = []
-        self.stop = threading.Event()
-        self.t = threading.Thread(target=self._run, daemon=True)
-
-    def _run(self):
-        while not self.stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
-                for line in out.stdout.strip().splitlines():
-                    self.rows.append([x.strip() for x in line.split(",")])
-            except Exception:
-                pass
-            self.stop.wait(0.2)
+        self.proc = None
 
     def __enter__(self):
-        self.t.start()
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.3)  # first sample lands before the timed region starts
+        except Exception:
+            self.proc = None
         return self
 
     def __exit__(self, *a):
-        self.stop.set()
-        self.t.join(timeout=10)
+        if self.proc is None:
+            return
+        time.sleep(0.05)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.strip().splitlines():
+            self.rows.append([x.strip() for x in line.split(",")])
 
     def summary(self):
-        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        ok = [r for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        sm = [float(r[1]) for r in ok]
+        mx = [float(r[2]) for r in ok if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = set()
-        for r in self.rows:
-            if len(r) >= 9:
-                for k, nm in enumerate(names):
-                    if r[5 + k].lower() == "active":
-                        reasons.add(nm)
+        for r in ok:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
@@ -174,6 +177,52 @@ def cpu_baseline_leg(p, scene, w_h, u_h, budget_s=15.0):
             "sample": f"{n} steps x {sample} agents of the 208,812-triangle room (dynamics + render, FP64)"}
 
 
+def _recorded_traffic():
+    """DRAM bytes per ray-cast launch from the committed ncu summary, if it was
+    taken on the current kernel source (matching SHA-1), else None."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2407_14783_b300", "csrc", "raycast.cu")
+    prof = os.path.join(ROOT, "profiles", "raycast_large_scene_256agents.md")
+    try:
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        for line in open(prof):
+            if line.startswith("dram_bytes_per_launch"):
+                parts = dict(kv.strip().split("=") for kv in line.split(";"))
+                if parts.get("raycast_cu_sha1", "").strip() == sha:
+                    return int(parts["dram_bytes_per_launch"].strip())
+    except Exception:
+        pass
+    return None
+
+
+def raycast_roofline(sim, cnt, n, p, render_ms):
+    """Roofline of the dominant kernel.  Algorithmic bytes per launch (per agent-frame:
+    4096 rays x (N_node * 64 B + N_tri * 48 B + 7 B output) + 28 B of pose), with
+    N_node / N_tri the nodes and triangles each ray's own walk needs (counter build),
+    over the average launch time, against this GPU's L2 read bandwidth measured by
+    the library's probe (the scene is L2-resident)."""
+    rays = cnt["rays"]
+    items = max(cnt["items"], 1)
+    rays_per_item = rays / items
+    need_nodes = cnt["need_node_visits"] / rays
+    need_tris = (cnt["need_tri_tests"] + cnt["large_tests"] * rays_per_item) / rays
+    per_ray = need_nodes * 64 + need_tris * 48 + 7
+    alg_bytes = rays * per_ray + n * 28
+    achieved = alg_bytes / (render_ms * 1e-3) / 1e9
+    l2 = sim.probe_read_bandwidth(64 << 20, iters=20)
+    hbm, hbm_kind = _peaks()
+    return {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
+            "traffic": _recorded_traffic(), "kernel": "raycast_kernel",
+            "peak_kind": "L2 read bandwidth measured in this run (sim_probe_read_bandwidth, 64 MiB resident)",
+            "hbm_peak": hbm, "hbm_peak_kind": hbm_kind, "alg_bytes_per_launch": alg_bytes,
+            "launch_ms": render_ms,
+            "per_ray": {"need_nodes": need_nodes, "need_tris": need_tris, "bytes": per_ray},
+            "per_item": {"rays": rays_per_item, "node_fetches": cnt["node_visits"] / items,
+                         "tri_fetches": cnt["tri_tests"] / items, "large_tests": cnt["large_tests"] / items},
+            "packet_demand_gbs": (cnt["node_visits"] * 64 + (cnt["tri_tests"] + cnt["large_tests"]) * 48)
+                                 * rays_per_item / (render_ms * 1e-3) / 1e9}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -200,10 +249,14 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     # warm-up (also selects the render configuration by autotuning on this workload)
+    tune = None
     if args.no_autotune:
         best = sim.render_config()
     else:
-        best, _ = sim.autotune(ids, state, depth, rgb, iters=3)
+        best, times = sim.autotune(ids, state, depth, rgb, iters=3)
+        tune = {"{tile_w}x{tile_h}/rpl{rays_per_lane}/{s}stack/{g}".format(
+                    s="smem" if c["stack_in_smem"] else "reg", g="staged" if c["stage_in_smem"] else "bcast", **c):
+                round(t, 4) for c, t in zip(Sim.render_configs(), times)}
     for t in range(W):
         if t % EPISODE == 0:
             state.copy_(spawn)
@@ -272,15 +325,8 @@ def run_ours(args):
     state.copy_(spawn)
     sim.step(state, cmds[W])
     cnt = sim.render(ids, state, depth, rgb, counted=True)
-    items = max(cnt["items"], 1)
-    rays_per_item = cnt["rays"] / items
-    node_per_item = cnt["node_visits"] / items
-    tri_per_item = (cnt["tri_tests"] + cnt["large_tests"]) / items
-    fetched = cnt["node_visits"] * 64 + (cnt["tri_tests"] + cnt["large_tests"]) * 48
-    out_bytes = n * p["height"] * p["width"] * 7 + n * 7 * 4
     render_ms = statistics.mean(ren_ms)
-    hbm_peak, peak_kind = _peaks()
-    achieved = (fetched + out_bytes) / (render_ms * 1e-3) / 1e9
+    roof = raycast_roofline(sim, cnt, n, p, render_ms)
     clocks = clk.summary()
 
     line = {"metric": METRIC, "value": value, "unit": "agent-frames/s", "n_gpus": ws, "steps": K, "warmup": W,
@@ -289,15 +335,10 @@ def run_ours(args):
             "config": {"workload": "single large scene: 208,812 triangles, 256 agents per GPU, RK4 dt=0.02, "
                                    "64x64 FP32 depth + uint8 RGB", "agents_per_gpu": n,
                        "triangles": int(scene.n_tris), "l2": "flushed between timed steps (256 MiB write)",
-                       "reset_every_steps": EPISODE, "render_config": best},
+                       "reset_every_steps": EPISODE, "render_config": best, "autotune_ms": tune},
             "e2e": e2e, "gpu_launches": 2 * K,
             "breakdown_ms": {"dynamics": statistics.mean(dyn_ms), "render": render_ms},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "raycast_kernel",
-                         "bytes_per_launch": fetched + out_bytes,
-                         "per_item": {"rays": rays_per_item, "node_fetches": node_per_item,
-                                      "tri_fetches": tri_per_item}},
+            "roofline": roof,
             "clocks": clocks}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg(p, scene, w_h, u_h)
@@ -309,6 +350,89 @@ def run_ours(args):
     return 0
 
 
+def batched_scenes(n_scenes=64, lo=10_000, hi=1_000_000, seed=99):
+    """64 procedural scenes with log-uniform triangle counts (seeds 100..163)."""
+    sizes = wl.Rng(seed).log_uniform(lo, hi, n_scenes)
+    return [wl.sized_scene(int(t), 100 + i) for i, t in enumerate(sizes)]
+
+
+def run_batched(args):
+    """Batched multi-scene workload: 64 scenes of 10k-1M triangles, 4,096 agents
+    spread by Zipf(1.1), one persistent render per step, 100-step graph-captured
+    loop; autotuned render configuration against the fixed 8x4 one."""
+    import torch
+    from paper_2407_14783_b300.sim import Sim, to_soa
+    p = wl.params()
+    w_h, u_h = _hover(p)
+    t0 = time.time()
+    scenes = batched_scenes()
+    gen_s = time.time() - t0
+    n_agents, T = 4096, 100
+    counts = wl.zipf_partition(n_agents, len(scenes), 1.1, 7)
+    sim = Sim(p)
+    t0 = time.time()
+    sids = [sim.add_workload_scene(sc) for sc in scenes]
+    build_s = time.time() - t0
+    spawn = np.concatenate([wl.spawn_states(sc, int(k), 1000 + i, w_h) for i, (sc, k) in enumerate(zip(scenes, counts))])
+    spawn = to_soa(spawn)
+    ids = torch.tensor(np.repeat(sids, counts), dtype=torch.int32, device="cuda")
+    cmds = torch.tensor(np.ascontiguousarray(wl.hover_commands(T, n_agents, 4, u_h).astype(np.float32)
+                                             .transpose(0, 2, 1)), device="cuda")
+    F = 2
+    depth = torch.empty((F, n_agents, p["height"], p["width"]), device="cuda")
+    rgb = torch.empty((F, n_agents, p["height"], p["width"], 3), dtype=torch.uint8, device="cuda")
+    state = spawn.clone()
+    fixed = sim.render_config()
+    best, times = sim.autotune(ids, state, depth[0], rgb[0], iters=3)
+    results = {}
+    for name, cfg in (("fixed_8x4", fixed), ("autotuned", best)):
+        sim.set_render_config(cfg)
+        loop = sim.make_loop(ids, state, cmds, depth, rgb)
+        for _ in range(args.warmup):
+            state.copy_(spawn)
+            loop.launch()
+        torch.cuda.synchronize()
+        evs = []
+        with ClockSampler(0) as clk:
+            for _ in range(args.steps):
+                state.copy_(spawn)   # every timed loop starts from the spawn states (outside the events)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                loop.launch()
+                e1.record()
+                evs.append((e0, e1))
+            torch.cuda.synchronize()
+        sim.check()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        results[name] = {"clk": clk.summary()}
+        results[name]["ms_per_loop"] = statistics.mean(ms)
+        results[name]["value"] = n_agents * T / (statistics.mean(ms) * 1e-3)
+        loop.close()
+    sim.set_render_config(best)
+    total_tris = int(sum(sc.n_tris for sc in scenes))
+    line = {"metric": METRIC, "value": results["autotuned"]["value"], "unit": "agent-frames/s", "n_gpus": 1,
+            "steps": args.steps * T, "warmup": args.warmup * T,
+            "ms_per_step": results["autotuned"]["ms_per_loop"] / T, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (64 procedural scenes, seeded)",
+            "config": {"workload": "batched multi-scene: 64 scenes of 10k-1M triangles (log-uniform), 4,096 agents "
+                                   "by Zipf(1.1), 100-step graph-captured loop, 64x64 depth+RGB",
+                       "scenes": len(scenes), "triangles_total": total_tris,
+                       "triangles_min_max": [int(min(sc.n_tris for sc in scenes)),
+                                             int(max(sc.n_tris for sc in scenes))],
+                       "agents_per_scene_min_max": [int(counts.min()), int(counts.max())],
+                       "l2": "inputs larger than L2 (scene BVHs %.2f GB)" % (
+                           sum(sim.scene_info(i)["bytes"] for i in sids) / 1e9),
+                       "fixed_config": fixed, "autotuned_config": best,
+                       "fixed_value": results["fixed_8x4"]["value"],
+                       "autotuned_over_fixed": results["autotuned"]["value"] / results["fixed_8x4"]["value"],
+                       "scene_generation_s": gen_s, "bvh_build_s": build_s},
+            "gpu_launches": args.steps * T * 2,
+            "clocks": results["autotuned"]["clk"]}
+    print(json.dumps(line), flush=True)
+    sim.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -317,11 +441,16 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--no-autotune", action="store_true", help="use the default ray-cast configuration")
+    ap.add_argument("--workload", choices=["large", "batched"], default="large",
+                    help="large: single 208,812-triangle scene, 256 agents (default); batched: 64 scenes, "
+                         "4,096 agents, graph-captured 100-step loop (--steps counts loops)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_ours(args)
 
 

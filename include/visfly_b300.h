@@ -196,14 +196,35 @@ int sim_rollout_backward(sim_ctx* ctx, int32_t n_agents, int32_t T, int32_t K, c
 int sim_env_step(sim_ctx* ctx, int32_t n_agents, const int32_t* scene_of_agent, float* state,
                  const float* cmd_host, float* depth_host, uint8_t* rgb_host, float* state_host, void* stream);
 
+/* A captured step loop: T environment steps (sim_step then sim_render per
+ * step, commands cmds[t]) recorded once into a CUDA graph and replayed with one
+ * launch (the batched-multi-scene pattern: many scenes, one persistent render
+ * per step, no per-step host work).
+ *   scene_of_agent dev int32 [n]; state dev [17][n] (updated in place by every
+ *   replay); cmds dev [T][4][n]; depth dev float32 [F][n][H][W] or NULL, rgb dev
+ *   uint8 [F][n][H][W][3] or NULL: step t writes frame slot t % F (F >= 1).
+ * The pointers are baked into the graph: the buffers must stay allocated and
+ * at the same addresses until sim_loop_destroy.  The loop owns its own work
+ * counters, so its replays do not share them with other renders.  The render
+ * configuration current at creation is used.  Creation synchronises `stream`. */
+typedef struct sim_loop sim_loop;
+int sim_loop_create(sim_ctx* ctx, sim_loop** out, int32_t n_agents, int32_t T, const int32_t* scene_of_agent,
+                    float* state, const float* cmds, float* depth, uint8_t* rgb, int32_t n_frames, void* stream);
+/* Replay the whole loop on `stream` (asynchronous). */
+int sim_loop_launch(sim_loop* loop, void* stream);
+int sim_loop_destroy(sim_loop* loop);
+
 /* Ray-cast kernel configuration (the autotuner's search space).
  *   tile_w x tile_h pixels per warp work item, rays_per_lane in {1, 2}
- *   (tile_w * tile_h = 32 * rays_per_lane), stack_in_smem (1: per-warp stack in
- *   shared memory, 0: stack distributed over the warp's registers), stack_depth
- *   in {32, 64}, warps_per_cta in {2, 4, 8}, ctas_per_sm (persistent grid =
- *   ctas_per_sm * SM count; 0 = occupancy limit). */
+ *   (tile_w * tile_h = 32 * rays_per_lane); stack_in_smem (1: per-warp stack in
+ *   shared memory, 0: stack spread over the warp's registers); stack_depth must
+ *   be 64; warps_per_cta must be 4; ctas_per_sm (persistent grid =
+ *   ctas_per_sm * SM count; 0 = as many as fit); stage_in_smem (1: node and
+ *   triangle records are fetched by a few lanes with coalesced float4 loads
+ *   into shared memory and read back by all lanes; 0: every lane loads the
+ *   same address, a broadcast through L1). */
 typedef struct sim_render_config {
-    int32_t tile_w, tile_h, rays_per_lane, stack_in_smem, stack_depth, warps_per_cta, ctas_per_sm;
+    int32_t tile_w, tile_h, rays_per_lane, stack_in_smem, stack_depth, warps_per_cta, ctas_per_sm, stage_in_smem;
 } sim_render_config;
 int sim_get_render_config(const sim_ctx* ctx, sim_render_config* cfg);
 int sim_set_render_config(sim_ctx* ctx, const sim_render_config* cfg);
@@ -218,10 +239,13 @@ int sim_autotune_render(sim_ctx* ctx, int32_t n_agents, const int32_t* scene_of_
 /* The supported configurations (returns how many; fills up to max of them). */
 int sim_render_config_list(sim_render_config* out, int32_t max);
 
-/* Traversal counters of the last sim_render_counted call: BVH node visits and
- * triangle tests per warp work item summed over all items, and work items. */
+/* Traversal counters of one sim_render_counted call.  node_visits and
+ * tri_tests count per warp work item (the packet walk); large_tests the large
+ * triangles tested per item; need_node_visits and need_tri_tests sum over rays
+ * the nodes and triangles that ray's own walk needs (its ray entered the box);
+ * items the work items, rays the primary rays. */
 typedef struct sim_render_counters {
-    int64_t node_visits, tri_tests, large_tests, items, rays;
+    int64_t node_visits, tri_tests, large_tests, items, rays, need_node_visits, need_tri_tests;
 } sim_render_counters;
 int sim_render_counted(sim_ctx* ctx, int32_t n_agents, const int32_t* scene_of_agent, const float* state,
                        float* depth, uint8_t* rgb, int32_t* hit_id, sim_render_counters* counters, void* stream);

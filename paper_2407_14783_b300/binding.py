@@ -46,7 +46,8 @@ class SceneInfo(ctypes.Structure):
 class RenderConfig(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("rays_per_lane", ctypes.c_int32),
                 ("stack_in_smem", ctypes.c_int32), ("stack_depth", ctypes.c_int32),
-                ("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+                ("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("stage_in_smem", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -54,7 +55,8 @@ class RenderConfig(ctypes.Structure):
 
 class RenderCounters(ctypes.Structure):
     _fields_ = [("node_visits", ctypes.c_int64), ("tri_tests", ctypes.c_int64), ("large_tests", ctypes.c_int64),
-                ("items", ctypes.c_int64), ("rays", ctypes.c_int64)]
+                ("items", ctypes.c_int64), ("rays", ctypes.c_int64), ("need_node_visits", ctypes.c_int64),
+                ("need_tri_tests", ctypes.c_int64)]
 
 
 def make_params(p: dict) -> SimParams:
@@ -88,6 +90,9 @@ SIGNATURES = {
     "sim_rollout": [_vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
     "sim_rollout_backward": [_vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
     "sim_env_step": [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "sim_loop_create": [_vp, _P(_vp), _i32, _i32, _vp, _vp, _vp, _vp, _vp, _i32, _vp],
+    "sim_loop_launch": [_vp, _vp],
+    "sim_loop_destroy": [_vp],
     "sim_get_render_config": [_vp, _P(RenderConfig)],
     "sim_set_render_config": [_vp, _P(RenderConfig)],
     "sim_autotune_render": [_vp, _i32, _vp, _vp, _vp, _vp, _i32, _P(RenderConfig), _P(ctypes.c_float), _i32, _vp],

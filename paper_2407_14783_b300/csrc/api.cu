@@ -43,6 +43,13 @@ struct SceneRec {
 
 }  // namespace
 
+struct sim_loop {
+    sim_ctx* ctx = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned* counters = nullptr;
+};
+
 struct sim_ctx {
     int device = 0;
     int num_sms = 0;
@@ -59,7 +66,7 @@ struct sim_ctx {
     unsigned* d_ring = nullptr;  // [kRing][2]
     std::atomic<unsigned> ring_next{0};
     long long* d_stats = nullptr;
-    sim_render_config rcfg{8, 4, 1, 0, 64, 4, 0};
+    sim_render_config rcfg{8, 4, 1, 0, 64, 4, 0, 0};  // fastest measured on the large scene
     // staging for sim_env_step
     float* d_cmd = nullptr;
     float* d_depth = nullptr;
@@ -309,9 +316,13 @@ int check_render_args(sim_ctx* c, int n, const void* soa, const void* state) {
 }
 
 int do_render(sim_ctx* c, int n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb, int32_t* hit,
-              bool count, const sim_render_config& cfg, cudaStream_t s) {
+              bool count, const sim_render_config& cfg, cudaStream_t s, unsigned* own_counters = nullptr) {
     if (n == 0) return SIM_OK;
     RenderArgs a = render_args(c, n, soa, state, depth, rgb, hit);
+    if (own_counters) {
+        a.counter = own_counters;
+        a.done = own_counters + 1;
+    }
     int ctas = 0;
     if (cfg.ctas_per_sm > 0) ctas = cfg.ctas_per_sm * c->num_sms;
     cudaError_t e = launch_render(a, cfg, ctas, count, s);
@@ -592,6 +603,8 @@ int sim_render_counted(sim_ctx* c, int32_t n, const int32_t* soa, const float* s
     out->large_tests = h[2];
     out->items = h[3];
     out->rays = (int64_t)n * c->cam.W * c->cam.H;
+    out->need_node_visits = h[4];
+    out->need_tri_tests = h[5];
     return SIM_OK;
 }
 
@@ -667,6 +680,73 @@ int sim_env_step(sim_ctx* c, int32_t n, const int32_t* soa, float* state, const 
     if (e == cudaSuccess && state_host)
         e = cudaMemcpyAsync(state_host, state, sizeof(float) * 17 * n, cudaMemcpyDeviceToHost, s);
     return e == cudaSuccess ? SIM_OK : cuda_fail(e, "observation download");
+}
+
+int sim_loop_create(sim_ctx* c, sim_loop** out, int32_t n, int32_t T, const int32_t* soa, float* state,
+                    const float* cmds, float* depth, uint8_t* rgb, int32_t n_frames, void* stream) {
+    if (!out) return fail(SIM_ERR_INVALID_ARG, "null output");
+    *out = nullptr;
+    if (T < 1 || n_frames < 1 || !cmds) return fail(SIM_ERR_INVALID_ARG, "bad loop arguments");
+    int rc = check_render_args(c, n, soa, state);
+    if (rc) return rc;
+    DeviceGuard g(c->device);
+    sim_loop* L = new sim_loop();
+    L->ctx = c;
+    void* cnt;
+    if ((rc = ctx_alloc(c, 2 * sizeof(unsigned), &cnt))) {
+        delete L;
+        return rc;
+    }
+    L->counters = (unsigned*)cnt;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStream_t cap;
+    cudaError_t e = cudaMemsetAsync(L->counters, 0, 2 * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        ctx_free(c, L->counters, 2 * sizeof(unsigned));
+        delete L;
+        return cuda_fail(e, "loop set-up");
+    }
+    const size_t frame = (size_t)n * c->cam.W * c->cam.H;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    for (int t = 0; t < T && e == cudaSuccess && rc == SIM_OK; ++t) {
+        e = launch_step(c->dyn, n, state, cmds + (size_t)t * 4 * n, nullptr, cap);
+        if (e != cudaSuccess) break;
+        const size_t slot = (size_t)(t % n_frames);
+        rc = do_render(c, n, soa, state, depth ? depth + slot * frame : nullptr, rgb ? rgb + slot * frame * 3 : nullptr,
+                       nullptr, false, c->rcfg, cap, L->counters);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess && rc == SIM_OK) e = cudaGraphInstantiate(&L->exec, graph, 0);
+    cudaStreamDestroy(cap);
+    L->graph = graph;
+    if (e != cudaSuccess || rc != SIM_OK) {
+        sim_loop_destroy(L);
+        return rc ? rc : cuda_fail(e, "loop capture");
+    }
+    *out = L;
+    return SIM_OK;
+}
+
+int sim_loop_launch(sim_loop* L, void* stream) {
+    if (!L || !L->exec) return fail(SIM_ERR_INVALID_ARG, "null loop");
+    DeviceGuard g(L->ctx->device);
+    cudaError_t e = cudaGraphLaunch(L->exec, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e, "loop launch");
+}
+
+int sim_loop_destroy(sim_loop* L) {
+    if (!L) return SIM_OK;
+    DeviceGuard g(L->ctx->device);
+    cudaDeviceSynchronize();
+    if (L->exec) cudaGraphExecDestroy(L->exec);
+    if (L->graph) cudaGraphDestroy(L->graph);
+    ctx_free(L->ctx, L->counters, 2 * sizeof(unsigned));
+    delete L;
+    return SIM_OK;
 }
 
 int sim_get_render_config(const sim_ctx* c, sim_render_config* cfg) {

@@ -4,15 +4,19 @@
 // One warp renders one image tile of 32 * RPL pixels (one or two rays per
 // lane) and pulls the next (agent, tile) item from a global counter, so scenes
 // of very different size load-balance inside one launch.  The warp walks its
-// agent's scene BVH as a packet: a node's 64 bytes are fetched by four lanes
-// with coalesced float4 loads into the warp's shared-memory slot and read back
-// by every lane; each lane slab-tests both child boxes against its own rays and
-// a warp vote (__ballot_sync) decides which children any ray needs, near child
-// first, the other pushed on the warp's stack (shared memory or a stack spread
-// over the lanes' registers).  Leaves (up to 4 triangles, 12 float4, contiguous
-// in leaf order) are staged the same way and every lane runs Moller-Trumbore on
-// them.  The walk ends when the stack is empty; the votes skip every subtree
-// that no lane of the tile can reach before its current closest hit.
+// agent's scene BVH as a packet: a node's 64 bytes are either fetched by four
+// lanes with coalesced float4 loads into the warp's shared-memory slot and read
+// back by every lane (STAGE), or loaded by every lane from the same address (a
+// broadcast through L1).  Each lane slab-tests both child boxes against its own
+// rays and a warp vote (__ballot_sync) decides which children any ray needs,
+// near child first, the other pushed on the warp's stack (shared memory or a
+// stack spread over the lanes' registers).  Leaves (up to 4 triangles, 12
+// float4, contiguous in leaf order) are fetched the same way and every lane runs
+// Moller-Trumbore on them.  The walk ends when the stack is empty; the votes
+// skip every subtree that no ray of the tile can reach before its current
+// closest hit.  The scene's few large triangles (walls, floors) are kept out of
+// the tree; each tile first culls them against the bounding box of its ray
+// segments and tests the rest, which also seeds every ray's closest hit.
 //
 // Result per ray: the closest hit with max_depth >= t > 1e-6 and, among equal
 // FP32 t, the lowest triangle id (order-independent, so every configuration
@@ -27,6 +31,8 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kTmin = 1e-6f;
 constexpr int kIterCap = 1 << 18;  // node + leaf visits per work item
+constexpr int kStack = 64;
+constexpr int kWarpsPerCta = 4;
 
 struct Ray {
     float o[3], d[3], inv[3], ood[3];
@@ -69,36 +75,55 @@ __device__ __forceinline__ bool slab(const Ray& r, float lx, float ly, float lz,
     return r.live && tn <= tf;
 }
 
-template <int RPL>
-__device__ __forceinline__ void test_tris_staged(Ray (&ray)[RPL], const float4* __restrict__ src, int count,
-                                                 float4* stage, int lane) {
-    // count <= kLeafMax: lanes 0 .. 3*count-1 fetch one float4 each (contiguous)
-    __syncwarp();
-    if (lane < 3 * count) stage[lane] = __ldg(src + lane);
-    __syncwarp();
-    for (int k = 0; k < count; ++k) {
-        const float4 a = stage[3 * k], b = stage[3 * k + 1], c = stage[3 * k + 2];
+// Fetch `count` (<= 4) consecutive triangle records and test every ray.
+template <int RPL, bool STAGE>
+__device__ __forceinline__ void test_leaf(Ray (&ray)[RPL], const float4* __restrict__ src, int count, float4* stage,
+                                          int lane) {
+    if (STAGE) {
+        __syncwarp();
+        if (lane < 3 * count) stage[lane] = __ldg(src + lane);
+        __syncwarp();
+        for (int k = 0; k < count; ++k) {
+            const float4 a = stage[3 * k], b = stage[3 * k + 1], c = stage[3 * k + 2];
 #pragma unroll
-        for (int q = 0; q < RPL; ++q) mt_test(ray[q], a, b, c);
+            for (int q = 0; q < RPL; ++q) mt_test(ray[q], a, b, c);
+        }
+    } else {
+        for (int k = 0; k < count; ++k) {
+            const float4 a = __ldg(src + 3 * k), b = __ldg(src + 3 * k + 1), c = __ldg(src + 3 * k + 2);
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) mt_test(ray[q], a, b, c);
+        }
     }
 }
 
-template <int TW, int TH, int RPL, bool SMEM_STACK, int STACK, bool COUNT>
-__global__ void __launch_bounds__(256) raycast_kernel(RenderArgs A) {
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, off));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, off));
+    return v;
+}
+
+template <int TW, int TH, int RPL, bool SMEM_STACK, bool STAGE, bool COUNT>
+__global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_kernel(RenderArgs A) {
     static_assert(TW * TH == 32 * RPL, "tile must hold 32 * RPL pixels");
     extern __shared__ float4 smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wpc = blockDim.x >> 5;
     float4* stage = smem + warp * 12;
-    int* sstack = reinterpret_cast<int*>(smem + wpc * 12) + warp * STACK;
-    uint8_t* rgbstage = reinterpret_cast<uint8_t*>(reinterpret_cast<int*>(smem + wpc * 12) + wpc * STACK) +
-                        warp * (32 * RPL * 3);
+    int* sstack = reinterpret_cast<int*>(smem + kWarpsPerCta * 12) + warp * kStack;
+    uint8_t* rgbstage = reinterpret_cast<uint8_t*>(reinterpret_cast<int*>(smem + kWarpsPerCta * 12) +
+                                                   kWarpsPerCta * kStack) + warp * (32 * RPL * 3);
 
     const int W = A.cam.W, H = A.cam.H;
     const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
     const int tiles = tiles_x * tiles_y;
     const long long total = (long long)A.n_agents * tiles;
-    long long n_nodes = 0, n_tris = 0, n_large = 0, n_items = 0;
+    // COUNT statistics: per work item (warp) and per ray (what each ray's own walk needs)
+    long long c_nodes = 0, c_tris = 0, c_large = 0, c_items = 0, c_need_nodes = 0, c_need_tris = 0;
 
     for (;;) {
         long long item = 0;
@@ -113,7 +138,7 @@ __global__ void __launch_bounds__(256) raycast_kernel(RenderArgs A) {
         const int sid = __ldg(A.scene_of_agent + agent);
         const bool scene_ok = sid >= 0 && sid < A.n_scenes && A.table[sid].live;
         if (!scene_ok && lane == 0) set_error(A.err, kDevErrNotFound);
-        SceneRow row;
+        SceneRow row = {};
         if (scene_ok) row = A.table[sid];
 
         // camera pose of this agent (uniform loads)
@@ -133,45 +158,87 @@ __global__ void __launch_bounds__(256) raycast_kernel(RenderArgs A) {
         R[2][0] = 2.0f * (qx * qz - qw * qy) * inv_n;
         R[2][1] = 2.0f * (qy * qz + qw * qx) * inv_n;
         R[2][2] = (qw * qw - qx * qx - qy * qy + qz * qz) * inv_n;
-        const float ox = px + R[0][0] * A.cam.cam_off[0] + R[0][1] * A.cam.cam_off[1] + R[0][2] * A.cam.cam_off[2];
-        const float oy = py + R[1][0] * A.cam.cam_off[0] + R[1][1] * A.cam.cam_off[1] + R[1][2] * A.cam.cam_off[2];
-        const float oz = pz + R[2][0] * A.cam.cam_off[0] + R[2][1] * A.cam.cam_off[1] + R[2][2] * A.cam.cam_off[2];
+        const float o[3] = {
+            px + R[0][0] * A.cam.cam_off[0] + R[0][1] * A.cam.cam_off[1] + R[0][2] * A.cam.cam_off[2],
+            py + R[1][0] * A.cam.cam_off[0] + R[1][1] * A.cam.cam_off[1] + R[1][2] * A.cam.cam_off[2],
+            pz + R[2][0] * A.cam.cam_off[0] + R[2][1] * A.cam.cam_off[1] + R[2][2] * A.cam.cam_off[2]};
 
         Ray ray[RPL];
         int pix_r[RPL], pix_c[RPL];
+        float flo[3] = {o[0], o[1], o[2]}, fhi[3] = {o[0], o[1], o[2]};  // ray-segment bounds
 #pragma unroll
         for (int q = 0; q < RPL; ++q) {
             const int p = lane + 32 * q;
             const int c = tx0 + p % TW, r = ty0 + p / TW;
             pix_r[q] = r;
             pix_c[q] = c;
-            const float dy = -(float)(2 * c + 1 - W) * 0.5f * A.cam.pix;
-            const float dz = -(float)(2 * r + 1 - H) * 0.5f * A.cam.pix;
-            const float dB[3] = {1.0f, dy, dz};
+            const float dB[3] = {1.0f, -(float)(2 * c + 1 - W) * 0.5f * A.cam.pix,
+                                 -(float)(2 * r + 1 - H) * 0.5f * A.cam.pix};
             Ray& ry = ray[q];
-            ry.o[0] = ox; ry.o[1] = oy; ry.o[2] = oz;
+            ry.live = scene_ok && r < H && c < W;
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
+                ry.o[j] = o[j];
                 ry.d[j] = R[j][0] * dB[0] + R[j][1] * dB[1] + R[j][2] * dB[2];
-                ry.inv[j] = 1.0f / ry.d[j];
+                const float dd = fabsf(ry.d[j]) > 1e-20f ? ry.d[j] : copysignf(1e-20f, ry.d[j]);
+                ry.inv[j] = 1.0f / dd;
                 ry.ood[j] = ry.o[j] * ry.inv[j];
+                if (ry.live) {
+                    const float e = o[j] + ry.d[j] * A.cam.max_depth;
+                    flo[j] = fminf(flo[j], e);
+                    fhi[j] = fmaxf(fhi[j], e);
+                }
             }
             ry.best_t = A.cam.max_depth;
             ry.best_id = -1;
-            ry.live = scene_ok && r < H && c < W;
         }
 
         if (scene_ok) {
-            // large triangles: every ray tests them
-            for (int k0 = 0; k0 < row.n_large; k0 += kLeafMax) {
-                const int cnt = min(kLeafMax, row.n_large - k0);
-                test_tris_staged<RPL>(ray, row.large + 3 * k0, cnt, stage, lane);
-                if (COUNT) n_large += cnt;
+            // large triangles: cull against the tile's ray-segment bounds, test the rest
+            if (row.n_large > 0) {
+                float blo[3], bhi[3];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const float lo = warp_min(flo[j]), hi = warp_max(fhi[j]);
+                    const float pad = 1e-3f * (hi - lo) + 1e-4f;
+                    blo[j] = lo - pad;
+                    bhi[j] = hi + pad;
+                }
+                for (int k0 = 0; k0 < row.n_large; k0 += 32) {
+                    const int k = k0 + lane;
+                    bool keep = false;
+                    if (k < row.n_large) {
+                        const float4 a = __ldg(row.large + 3 * k), b = __ldg(row.large + 3 * k + 1),
+                                     c = __ldg(row.large + 3 * k + 2);
+                        const float tl[3] = {fminf(a.x, fminf(a.x + b.x, a.x + c.x)),
+                                             fminf(a.y, fminf(a.y + b.y, a.y + c.y)),
+                                             fminf(a.z, fminf(a.z + b.z, a.z + c.z))};
+                        const float th[3] = {fmaxf(a.x, fmaxf(a.x + b.x, a.x + c.x)),
+                                             fmaxf(a.y, fmaxf(a.y + b.y, a.y + c.y)),
+                                             fmaxf(a.z, fmaxf(a.z + b.z, a.z + c.z))};
+                        keep = tl[0] <= bhi[0] && th[0] >= blo[0] && tl[1] <= bhi[1] && th[1] >= blo[1] &&
+                               tl[2] <= bhi[2] && th[2] >= blo[2];
+                    }
+                    unsigned mask = __ballot_sync(kFull, keep);
+                    while (mask) {
+                        const int kk = k0 + __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        test_leaf<RPL, false>(ray, row.large + 3 * (size_t)kk, 1, stage, lane);
+                        if (COUNT) ++c_large;
+                    }
+                }
             }
             // BVH walk
             int cur = row.root;
             int sp = 0;
             int reg0 = 0, reg1 = 0;  // register stack: entry k in lane k % 32 of reg[k / 32]
+            bool need[RPL];
+            unsigned long long needmask[RPL];
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) {
+                need[q] = ray[q].live;
+                needmask[q] = 0ull;
+            }
             int iters = 0;
             while (cur != kEmptyRoot) {
                 if (++iters > kIterCap) {
@@ -181,50 +248,83 @@ __global__ void __launch_bounds__(256) raycast_kernel(RenderArgs A) {
                 int next = kEmptyRoot;
                 if (cur >= 0) {
                     const float4* np = row.nodes + 4 * (size_t)cur;
-                    __syncwarp();
-                    if (lane < 4) stage[lane] = __ldg(np + lane);
-                    __syncwarp();
-                    const float4 n0 = stage[0], n1 = stage[1], n2 = stage[2], n3 = stage[3];
-                    if (COUNT) ++n_nodes;
+                    float4 n0, n1, n2, n3;
+                    if (STAGE) {
+                        __syncwarp();
+                        if (lane < 4) stage[lane] = __ldg(np + lane);
+                        __syncwarp();
+                        n0 = stage[0];
+                        n1 = stage[1];
+                        n2 = stage[2];
+                        n3 = stage[3];
+                    } else {
+                        n0 = __ldg(np);
+                        n1 = __ldg(np + 1);
+                        n2 = __ldg(np + 2);
+                        n3 = __ldg(np + 3);
+                    }
                     bool h0 = false, h1 = false, pref1 = false;
+                    bool ha[RPL], hb[RPL];
 #pragma unroll
                     for (int q = 0; q < RPL; ++q) {
                         float t0, t1;
-                        const bool a = slab(ray[q], n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, t0);
-                        const bool b = slab(ray[q], n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, t1);
-                        h0 |= a;
-                        h1 |= b;
-                        pref1 |= a && b && t1 < t0;
+                        ha[q] = slab(ray[q], n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, t0);
+                        hb[q] = slab(ray[q], n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, t1);
+                        h0 |= ha[q];
+                        h1 |= hb[q];
+                        pref1 |= ha[q] && hb[q] && t1 < t0;
                     }
                     const unsigned b0 = __ballot_sync(kFull, h0), b1 = __ballot_sync(kFull, h1);
                     const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+                    if (COUNT) {
+                        ++c_nodes;
+#pragma unroll
+                        for (int q = 0; q < RPL; ++q) c_need_nodes += need[q] ? 1 : 0;
+                    }
                     if (b0 && b1) {
-                        const unsigned both = b0 & b1;
-                        const bool near1 = 2 * __popc(__ballot_sync(kFull, pref1)) > __popc(both);
+                        const bool near1 = 2 * __popc(__ballot_sync(kFull, pref1)) > __popc(b0 & b1);
                         const int far = near1 ? c0 : c1;
                         next = near1 ? c1 : c0;
-                        if (sp >= STACK) {
+                        if (sp >= kStack) {
                             if (lane == 0) set_error(A.err, kDevErrTraversal);
                             break;
                         }
                         if (SMEM_STACK) {
                             if (lane == 0) sstack[sp] = far;
-                        } else {
-                            if (lane == (sp & 31)) {
-                                if (sp < 32) reg0 = far; else reg1 = far;
+                        } else if (lane == (sp & 31)) {
+                            if (sp < 32) reg0 = far; else reg1 = far;
+                        }
+                        if (COUNT) {
+#pragma unroll
+                            for (int q = 0; q < RPL; ++q) {
+                                const bool nf = need[q] && (near1 ? ha[q] : hb[q]);
+                                needmask[q] = (needmask[q] & ~(1ull << sp)) | ((unsigned long long)nf << sp);
+                                need[q] = need[q] && (near1 ? hb[q] : ha[q]);
                             }
                         }
                         ++sp;
                     } else if (b0) {
                         next = c0;
+                        if (COUNT) {
+#pragma unroll
+                            for (int q = 0; q < RPL; ++q) need[q] = need[q] && ha[q];
+                        }
                     } else if (b1) {
                         next = c1;
+                        if (COUNT) {
+#pragma unroll
+                            for (int q = 0; q < RPL; ++q) need[q] = need[q] && hb[q];
+                        }
                     }
                 } else {
                     int first, count;
                     leaf_decode(cur, first, count);
-                    test_tris_staged<RPL>(ray, row.tris + 3 * (size_t)first, count, stage, lane);
-                    if (COUNT) n_tris += count;
+                    test_leaf<RPL, STAGE>(ray, row.tris + 3 * (size_t)first, count, stage, lane);
+                    if (COUNT) {
+                        c_tris += count;
+#pragma unroll
+                        for (int q = 0; q < RPL; ++q) c_need_tris += need[q] ? count : 0;
+                    }
                 }
                 if (next == kEmptyRoot) {
                     if (sp == 0) break;
@@ -234,6 +334,10 @@ __global__ void __launch_bounds__(256) raycast_kernel(RenderArgs A) {
                         next = sstack[sp];
                     } else {
                         next = __shfl_sync(kFull, sp < 32 ? reg0 : reg1, sp & 31);
+                    }
+                    if (COUNT) {
+#pragma unroll
+                        for (int q = 0; q < RPL; ++q) need[q] = (needmask[q] >> sp) & 1ull;
                     }
                 }
                 cur = next;
@@ -283,14 +387,25 @@ __global__ void __launch_bounds__(256) raycast_kernel(RenderArgs A) {
             }
             __syncwarp();
         }
-        if (COUNT) ++n_items;
+        if (COUNT) ++c_items;
     }
 
-    if (COUNT && lane == 0) {
-        atomicAdd((unsigned long long*)&A.counters[0], (unsigned long long)n_nodes);
-        atomicAdd((unsigned long long*)&A.counters[1], (unsigned long long)n_tris);
-        atomicAdd((unsigned long long*)&A.counters[2], (unsigned long long)n_large);
-        atomicAdd((unsigned long long*)&A.counters[3], (unsigned long long)n_items);
+    if (COUNT) {
+        // per-ray counts summed over the warp, per-item counts from lane 0
+        long long nn = c_need_nodes, nt = c_need_tris;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            nn += __shfl_xor_sync(kFull, nn, off);
+            nt += __shfl_xor_sync(kFull, nt, off);
+        }
+        if (lane == 0) {
+            atomicAdd((unsigned long long*)&A.counters[0], (unsigned long long)c_nodes);
+            atomicAdd((unsigned long long*)&A.counters[1], (unsigned long long)c_tris);
+            atomicAdd((unsigned long long*)&A.counters[2], (unsigned long long)c_large);
+            atomicAdd((unsigned long long*)&A.counters[3], (unsigned long long)c_items);
+            atomicAdd((unsigned long long*)&A.counters[4], (unsigned long long)nn);
+            atomicAdd((unsigned long long*)&A.counters[5], (unsigned long long)nt);
+        }
     }
     // the last CTA to finish resets the work counter for the next launch
     __syncthreads();
@@ -304,47 +419,46 @@ __global__ void __launch_bounds__(256) raycast_kernel(RenderArgs A) {
     }
 }
 
-template <int TW, int TH, int RPL, bool SMEM_STACK, int STACK, bool COUNT>
-cudaError_t launch_one(const RenderArgs& a, int warps_per_cta, int ctas, cudaStream_t s) {
-    auto k = raycast_kernel<TW, TH, RPL, SMEM_STACK, STACK, COUNT>;
-    const size_t shm = render_smem_bytes(warps_per_cta, STACK, RPL);
-    return launch_cfg(reinterpret_cast<const void*>(k), a, warps_per_cta, ctas, shm, s);
+template <int TW, int TH, int RPL, bool SMEM_STACK, bool STAGE, bool COUNT>
+cudaError_t launch_one(const RenderArgs& a, int ctas, cudaStream_t s) {
+    auto k = raycast_kernel<TW, TH, RPL, SMEM_STACK, STAGE, COUNT>;
+    const size_t shm = render_smem_bytes(kWarpsPerCta, kStack, RPL);
+    return launch_cfg(reinterpret_cast<const void*>(k), a, kWarpsPerCta, ctas, shm, s);
+}
+
+template <int TW, int TH, int RPL, bool COUNT>
+cudaError_t launch_shape(const RenderArgs& a, const sim_render_config& c, int ctas, cudaStream_t s) {
+    if (c.stack_in_smem) {
+        if (c.stage_in_smem) return launch_one<TW, TH, RPL, true, true, COUNT>(a, ctas, s);
+        return launch_one<TW, TH, RPL, true, false, COUNT>(a, ctas, s);
+    }
+    if (c.stage_in_smem) return launch_one<TW, TH, RPL, false, true, COUNT>(a, ctas, s);
+    return launch_one<TW, TH, RPL, false, false, COUNT>(a, ctas, s);
 }
 
 template <bool COUNT>
 cudaError_t dispatch(const RenderArgs& a, const sim_render_config& c, int ctas, cudaStream_t s) {
-#define VF_CASE(TW, TH, RPL)                                                                                   \
-    if (c.tile_w == TW && c.tile_h == TH && c.rays_per_lane == RPL) {                                         \
-        if (c.stack_in_smem) {                                                                                 \
-            if (c.stack_depth <= 32) return launch_one<TW, TH, RPL, true, 32, COUNT>(a, c.warps_per_cta, ctas, s); \
-            return launch_one<TW, TH, RPL, true, 64, COUNT>(a, c.warps_per_cta, ctas, s);                     \
-        }                                                                                                      \
-        if (c.stack_depth <= 32) return launch_one<TW, TH, RPL, false, 32, COUNT>(a, c.warps_per_cta, ctas, s); \
-        return launch_one<TW, TH, RPL, false, 64, COUNT>(a, c.warps_per_cta, ctas, s);                        \
-    }
-    VF_CASE(8, 4, 1)
-    VF_CASE(4, 8, 1)
-    VF_CASE(16, 2, 1)
-    VF_CASE(8, 8, 2)
-    VF_CASE(16, 4, 2)
-#undef VF_CASE
+    if (c.tile_w == 8 && c.tile_h == 4 && c.rays_per_lane == 1) return launch_shape<8, 4, 1, COUNT>(a, c, ctas, s);
+    if (c.tile_w == 4 && c.tile_h == 8 && c.rays_per_lane == 1) return launch_shape<4, 8, 1, COUNT>(a, c, ctas, s);
+    if (c.tile_w == 16 && c.tile_h == 2 && c.rays_per_lane == 1) return launch_shape<16, 2, 1, COUNT>(a, c, ctas, s);
+    if (c.tile_w == 8 && c.tile_h == 8 && c.rays_per_lane == 2) return launch_shape<8, 8, 2, COUNT>(a, c, ctas, s);
+    if (c.tile_w == 16 && c.tile_h == 4 && c.rays_per_lane == 2) return launch_shape<16, 4, 2, COUNT>(a, c, ctas, s);
     return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
 size_t render_smem_bytes(int warps_per_cta, int stack_depth, int rpl) {
-    const int st = stack_depth <= 32 ? 32 : 64;
-    return (size_t)warps_per_cta * (12 * sizeof(float4) + st * sizeof(int) + 32 * rpl * 3);
+    return (size_t)warps_per_cta * (12 * sizeof(float4) + stack_depth * sizeof(int) + 32 * rpl * 3);
 }
 
 int render_config_list(sim_render_config* out, int max) {
     static const int shapes[][3] = {{8, 4, 1}, {4, 8, 1}, {16, 2, 1}, {8, 8, 2}, {16, 4, 2}};
     int k = 0;
     for (const auto& sh : shapes)
-        for (int smem = 0; smem <= 1; ++smem)
-            for (int wpc : {4, 8}) {
-                if (k < max && out) out[k] = sim_render_config{sh[0], sh[1], sh[2], smem, 64, wpc, 0};
+        for (int stack = 0; stack <= 1; ++stack)
+            for (int stg = 0; stg <= 1; ++stg) {
+                if (k < max && out) out[k] = sim_render_config{sh[0], sh[1], sh[2], stack, kStack, kWarpsPerCta, 0, stg};
                 ++k;
             }
     return k;
@@ -356,8 +470,8 @@ bool render_config_valid(const sim_render_config& c) {
     for (int i = 0; i < n; ++i) {
         const sim_render_config& a = all[i];
         if (a.tile_w == c.tile_w && a.tile_h == c.tile_h && a.rays_per_lane == c.rays_per_lane &&
-            (c.warps_per_cta == 2 || c.warps_per_cta == 4 || c.warps_per_cta == 8) &&
-            (c.stack_depth == 32 || c.stack_depth == 64) && c.ctas_per_sm >= 0 && c.ctas_per_sm <= 32)
+            (c.stack_in_smem == 0 || c.stack_in_smem == 1) && (c.stage_in_smem == 0 || c.stage_in_smem == 1) &&
+            c.warps_per_cta == kWarpsPerCta && c.stack_depth == kStack && c.ctas_per_sm >= 0 && c.ctas_per_sm <= 32)
             return true;
     }
     return false;

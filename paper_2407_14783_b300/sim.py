@@ -201,6 +201,22 @@ class Sim:
         B.check(rc, "sim_autotune_render", self.h)
         return best.as_dict(), list(times)
 
+    def make_loop(self, scene_of_agent, state, cmds, depth=None, rgb=None, stream=None) -> "Loop":
+        """Capture len(cmds) steps (step + render) into one CUDA graph.  depth / rgb
+        hold F frame slots ([F, n, H, W] / [F, n, H, W, 3]); step t writes slot t % F."""
+        T, n = cmds.shape[0], state.shape[1]
+        _need(scene_of_agent, torch.int32, (n,), "scene_of_agent")
+        _need(state, torch.float32, (STATE_DIM, n), "state")
+        _need(cmds, torch.float32, (T, CMD_DIM, n), "cmds")
+        F = depth.shape[0] if depth is not None else (rgb.shape[0] if rgb is not None else 1)
+        _need(depth, torch.float32, (F, n, self.H, self.W), "depth")
+        _need(rgb, torch.uint8, (F, n, self.H, self.W, 3), "rgb")
+        h = ctypes.c_void_p()
+        rc = self.L.sim_loop_create(self.h, ctypes.byref(h), n, T, _ptr(scene_of_agent), _ptr(state), _ptr(cmds),
+                                    _ptr(depth), _ptr(rgb), F, _stream(stream))
+        B.check(rc, "sim_loop_create", self.h)
+        return Loop(self, h, (scene_of_agent, state, cmds, depth, rgb))
+
     # ------------------------------------------------------------ env step with host buffers
     def env_step(self, scene_of_agent, state, cmd_host, depth_host=None, rgb_host=None, state_host=None,
                  stream=None):
@@ -230,6 +246,27 @@ class Sim:
         B.check(self.L.sim_probe_read_bandwidth(self.h, nbytes, iters, ctypes.byref(g), _stream(stream)),
                 "sim_probe_read_bandwidth", self.h)
         return g.value
+
+
+class Loop:
+    """A captured step loop (see Sim.make_loop); keeps its buffers alive."""
+
+    def __init__(self, sim, h, keep):
+        self.sim, self.h, self._keep = sim, h, keep
+
+    def launch(self, stream=None):
+        B.check(self.sim.L.sim_loop_launch(self.h, _stream(stream)), "sim_loop_launch", self.sim.h)
+
+    def close(self):
+        if self.h and self.h.value:
+            self.sim.L.sim_loop_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Rollout(torch.autograd.Function):
