@@ -433,6 +433,190 @@ def run_batched(args):
     return 0
 
 
+def run_diff(args):
+    """Differentiable rollout: 1,024 agents, 200 steps at dt = 0.02, checkpoints
+    every 10 steps; forward rollout kernel + hand-written adjoint kernel; loss =
+    squared distance to seeded goals + 0.01 * control effort.  Reports agent-steps/s
+    of forward + backward and the gradient error of sampled agents against the
+    FP64 oracle's exact gradient."""
+    import torch
+    from paper_2407_14783_b300.sim import Sim, to_soa
+    p = wl.params()
+    w_h, u_h = _hover(p)
+    scene = wl.cluttered_scene(seed=2)
+    n, T, K, lam = 1024, 200, 10, 0.01
+    s0 = wl.spawn_states(scene, n, 61, w_h).astype(np.float32)
+    U = wl.hover_commands(T, n, 62, u_h, rate_range=0.3).astype(np.float32)
+    goals = wl.goal_points(scene, n, 63).astype(np.float32)
+    sim = Sim(p)
+    st0 = to_soa(s0)
+    cm = torch.tensor(np.ascontiguousarray(U.transpose(0, 2, 1)), device="cuda")
+    g = torch.tensor(goals.T.copy(), device="cuda")
+    fw, bw = [], []
+    for it in range(args.warmup + args.steps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        states, ckpt, _ = sim.rollout(st0, cm, K=K)
+        e1.record()
+        gs = torch.zeros_like(states)
+        gs[1:, 0:3] = 2.0 * (states[1:, 0:3] - g[None]) / T
+        g0, gc = sim.rollout_backward(ckpt, cm, gs, K=K)
+        gc += 2.0 * lam * cm / T
+        e2.record()
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            fw.append(e0.elapsed_time(e1))
+            bw.append(e1.elapsed_time(e2))
+    sim.check()
+    import oracle
+    oracle.build()
+    pick = np.array([3, 517])
+    Lr, gsr, gur = oracle.rollout_loss_grad(p, s0[pick].astype(np.float64), U[:, pick].astype(np.float64),
+                                            goals[pick].astype(np.float64), lam)
+    g0n = g0.cpu().numpy().T
+    gcn = gc.cpu().numpy().transpose(0, 2, 1)
+    errs = []
+    for i, a in enumerate(pick):
+        full = np.concatenate([g0n[a], gcn[:, a].ravel()])
+        ref = np.concatenate([gsr[i], gur[:, i].ravel()])
+        errs.append(float(np.linalg.norm(full - ref) / np.linalg.norm(ref)))
+    ms = statistics.mean(fw) + statistics.mean(bw)
+    line = {"metric": "agent-steps/s (differentiable rollout: forward + adjoint) on 1 B300",
+            "value": n * T / (ms * 1e-3), "unit": "agent-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / T, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded spawns, goals, commands)",
+            "config": {"workload": "differentiable rollout: 1,024 agents, T=200, dt=0.02, checkpoint every 10 steps",
+                       "forward_ms": statistics.mean(fw), "backward_ms": statistics.mean(bw),
+                       "grad_rel_err_vs_fp64_oracle": errs, "l2": "state 1024 x 17 floats, L2-resident"},
+            "gpu_launches": 2}
+    print(json.dumps(line), flush=True)
+    sim.close()
+    return 0
+
+
+class _PinnedArena:
+    """Ring allocator over one pinned host buffer: request inputs and outputs
+    for the load generator (allocation blocks while the oldest live block is in
+    the way)."""
+
+    def __init__(self, nbytes):
+        import torch
+        self.buf = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+        self.size = nbytes
+        self.head = 0
+        self.live = []          # (start, end, ticket) in allocation order
+
+    def alloc(self, nbytes, release):
+        nbytes = (nbytes + 255) & ~255
+        if nbytes > self.size:
+            raise MemoryError("arena too small")
+        if self.head + nbytes > self.size:
+            self.head = 0
+        while self.live and self._overlaps(self.head, self.head + nbytes):
+            release(self.live.pop(0)[2])
+        start = self.head
+        self.head += nbytes
+        return start, start + nbytes
+
+    def _overlaps(self, a, b):
+        s, e, _ = self.live[0]
+        return a < e and s < b
+
+    def view(self, start, shape, dtype):
+        import torch
+        n = int(np.prod(shape)) * torch.tensor([], dtype=dtype).element_size()
+        return self.buf[start:start + n].view(dtype).view(*shape)
+
+
+def run_serving(args):
+    """Serving workload: 32 resident scenes of 50k-2M triangles; Poisson arrivals
+    (mean 2,000 requests/s at load 1.0), each request n ~ log-U[1, 1024] agents of one
+    scene for U{1..16} steps, returning the final state and the last 64x64
+    depth + RGB; throughput and p50 / p99 latency at loads 0.25, 0.5 and 1.0."""
+    import torch
+    from paper_2407_14783_b300.serve import Server
+    from paper_2407_14783_b300.sim import Sim
+    p = wl.params()
+    w_h, u_h = _hover(p)
+    t0 = time.time()
+    sizes = wl.Rng(5).log_uniform(50_000, 2_000_000, 32)
+    scenes = [wl.sized_scene(int(t), 500 + i) for i, t in enumerate(sizes)]
+    gen_s = time.time() - t0
+    sim = Sim(p)
+    sids = [sim.add_workload_scene(sc) for sc in scenes]
+    cap = 8192
+    srv = Server(sim, capacity=cap)
+    # per-scene pools of spawn states and commands (requests use the first n agents)
+    pool_s = [np.ascontiguousarray(wl.spawn_states(sc, 1024, 600 + i, w_h).astype(np.float32).T)
+              for i, sc in enumerate(scenes)]
+    pool_u = np.ascontiguousarray(wl.hover_commands(16, 1024, 7, u_h).astype(np.float32).transpose(0, 2, 1))
+    arena = _PinnedArena(6 << 30)
+    H, W = p["height"], p["width"]
+    rate = 2000.0
+    duration = float(args.serve_seconds)
+    levels = {}
+
+    lat = {}
+
+    def release(ticket):
+        if ticket not in lat:
+            lat[ticket] = srv.wait(ticket, 600000)
+
+    for li, load in enumerate((0.25, 0.5, 1.0)):
+        reqs = wl.poisson_requests(rate * load, duration, len(scenes), 50 + li)
+        arena.live.clear()
+        arena.head = 0
+        st0 = srv.stats()
+        tickets = []
+        start = time.perf_counter()
+        for q in reqs:
+            n, T = q["agents"], q["steps"]
+            nb = 4 * (17 * n + T * 4 * n + 17 * n + n * H * W) + 3 * n * H * W
+            delay = start + q["t"] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            a0, a1 = arena.alloc(nb, release)     # may wait for the oldest request in the way
+            off = a0
+            s0 = arena.view(off, (17, n), torch.float32); off += 4 * 17 * n
+            cm = arena.view(off, (T, 4, n), torch.float32); off += 4 * T * 4 * n
+            so = arena.view(off, (17, n), torch.float32); off += 4 * 17 * n
+            do = arena.view(off, (n, H, W), torch.float32); off += 4 * n * H * W
+            ro = arena.view(off, (n, H, W, 3), torch.uint8)
+            s0.copy_(torch.from_numpy(pool_s[q["scene"]][:, :n]))
+            cm.copy_(torch.from_numpy(pool_u[:T, :, :n]))
+            tk = srv.submit(sids[q["scene"]], s0, cm, so, do, ro, frames="last")
+            tickets.append(tk)
+            arena.live.append((a0, a1, tk))
+        for tk in tickets:
+            release(tk)
+        wall = time.perf_counter() - start
+        st1 = srv.stats()
+        lats = np.array([lat[t] for t in tickets])
+        frames = sum(q["agents"] * q["steps"] for q in reqs)
+        levels[str(load)] = {"offered_req_per_s": rate * load, "requests": len(reqs),
+                             "offered_agent_frames_per_s": frames / duration,
+                             "throughput_agent_frames_per_s": frames / wall,
+                             "p50_ms": float(np.percentile(lats, 50)), "p99_ms": float(np.percentile(lats, 99)),
+                             "mean_batch_agents": (st1["agent_frames"] - st0["agent_frames"]) /
+                                                  max(1, st1["iterations"] - st0["iterations"]),
+                             "wall_s": wall}
+    srv.close()
+    full = levels["1.0"]
+    line = {"metric": "agent-frames/s served (dynamics+64x64 depth/RGB) on 1 B300; p50/p99 step latency",
+            "value": full["throughput_agent_frames_per_s"], "unit": "agent-frames/s", "n_gpus": 1,
+            "steps": sum(v["requests"] for v in levels.values()), "warmup": 0,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (32 procedural scenes, Poisson request stream, seeded)",
+            "config": {"workload": "serving: 32 resident scenes of 50k-2M triangles, Poisson arrivals, "
+                                   "1-1024 agents x 1-16 steps per request, last 64x64 depth+RGB returned",
+                       "triangles_total": int(sum(sc.n_tris for sc in scenes)), "capacity_agents": cap,
+                       "seconds_per_load": duration, "scene_generation_s": gen_s},
+            "served": levels, "p50_ms": full["p50_ms"], "p99_ms": full["p99_ms"]}
+    print(json.dumps(line), flush=True)
+    sim.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -441,7 +625,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--no-autotune", action="store_true", help="use the default ray-cast configuration")
-    ap.add_argument("--workload", choices=["large", "batched"], default="large",
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="seconds of arrivals per load level")
+    ap.add_argument("--workload", choices=["large", "batched", "diff", "serving"], default="large",
                     help="large: single 208,812-triangle scene, 256 agents (default); batched: 64 scenes, "
                          "4,096 agents, graph-captured 100-step loop (--steps counts loops)")
     args = ap.parse_args()
@@ -451,6 +636,10 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "diff":
+        return run_diff(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

@@ -214,6 +214,57 @@ int sim_loop_create(sim_ctx* ctx, sim_loop** out, int32_t n_agents, int32_t T, c
 int sim_loop_launch(sim_loop* loop, void* stream);
 int sim_loop_destroy(sim_loop* loop);
 
+/* ---------------------------------------------------------------- serving
+ * A continuous-batching step server on one context.  Clients submit requests
+ * ("advance these n agents of scene s by k steps with these commands and give
+ * me the observations"); a server thread keeps scene BVHs and agent states on
+ * the device, admits queued requests between device iterations as agent slots
+ * and memory free up, packs every active request into one batch, and runs one
+ * dynamics launch and one persistent render launch per iteration, so requests
+ * of uneven size that arrive while others run share the GPU.  The environment
+ * step of Sec. III-C, served.  Results do not depend on what else is in the
+ * batch (agents never interact in this mode, Sec. III-B). */
+typedef struct sim_server sim_server;
+
+typedef struct sim_request {
+    int32_t scene_id;     /* resident scene */
+    int32_t n_agents;     /* 1 .. server capacity */
+    int32_t n_steps;      /* >= 1 */
+    int32_t frames;       /* 0: no images, 1: images of the last step, 2: images of every step */
+    const float* state0;  /* [17][n] host or device; read when the request is admitted */
+    const float* cmds;    /* [n_steps][4][n] host or device; read when the request is admitted */
+    float* state_out;     /* [17][n] final state, or NULL */
+    float* depth_out;     /* [n][H][W] (frames = 1) or [n_steps][n][H][W] (frames = 2), or NULL */
+    uint8_t* rgb_out;     /* same with a trailing [3], or NULL */
+} sim_request;
+
+/* capacity: most agents in one batch (1 .. 1<<20).  The server's batch buffers
+ * (two state buffers, commands, scene ids, one frame per agent slot) and each
+ * admitted request's device copy of its inputs come from the context's memory
+ * budget; a request that does not fit waits in the queue (memory admission). */
+int sim_server_create(sim_ctx* ctx, sim_server** out, int32_t capacity);
+/* Enqueue a request; *ticket identifies it.  The request's buffers must stay
+ * valid until sim_server_wait reports it finished.  INVALID_ARG when n_agents
+ * exceeds the capacity or the scene is not resident. */
+int sim_server_submit(sim_server* srv, const sim_request* req, int64_t* ticket);
+/* Wait up to timeout_ms (< 0: unbounded) for a request to finish.  SIM_OK with
+ * *latency_ms = completion - submission time; SIM_ERR_TIMEOUT if still running;
+ * SIM_ERR_NOT_FOUND for an unknown (or already collected) ticket; the
+ * request's own failure code otherwise (a cancelled request reports
+ * SIM_ERR_INVALID_ARG).  Collecting a finished request forgets the ticket. */
+int sim_server_wait(sim_server* srv, int64_t ticket, int32_t timeout_ms, double* latency_ms);
+/* Cancel a request that has not finished: queued requests are dropped, active
+ * ones leave the batch at the next iteration without writing outputs. */
+int sim_server_cancel(sim_server* srv, int64_t ticket);
+typedef struct sim_server_stats {
+    int64_t submitted, completed, cancelled, failed, iterations, agent_frames;
+    int64_t queued, active_requests, active_agents;
+    double mean_batch_agents;
+} sim_server_stats;
+int sim_server_stats_get(sim_server* srv, sim_server_stats* stats);
+/* Stop the server thread (pending requests are cancelled) and free its memory. */
+int sim_server_destroy(sim_server* srv);
+
 /* Ray-cast kernel configuration (the autotuner's search space).
  *   tile_w x tile_h pixels per warp work item, rays_per_lane in {1, 2}
  *   (tile_w * tile_h = 32 * rays_per_lane); stack_in_smem (1: per-warp stack in

@@ -59,6 +59,19 @@ class RenderCounters(ctypes.Structure):
                 ("need_tri_tests", ctypes.c_int64)]
 
 
+class SimRequest(ctypes.Structure):
+    _fields_ = [("scene_id", ctypes.c_int32), ("n_agents", ctypes.c_int32), ("n_steps", ctypes.c_int32),
+                ("frames", ctypes.c_int32), ("state0", ctypes.c_void_p), ("cmds", ctypes.c_void_p),
+                ("state_out", ctypes.c_void_p), ("depth_out", ctypes.c_void_p), ("rgb_out", ctypes.c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("cancelled", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("iterations", ctypes.c_int64), ("agent_frames", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("active_requests", ctypes.c_int64), ("active_agents", ctypes.c_int64),
+                ("mean_batch_agents", ctypes.c_double)]
+
+
 def make_params(p: dict) -> SimParams:
     s = SimParams()
     for name, ctype in SimParams._fields_:
@@ -93,6 +106,12 @@ SIGNATURES = {
     "sim_loop_create": [_vp, _P(_vp), _i32, _i32, _vp, _vp, _vp, _vp, _vp, _i32, _vp],
     "sim_loop_launch": [_vp, _vp],
     "sim_loop_destroy": [_vp],
+    "sim_server_create": [_vp, _P(_vp), _i32],
+    "sim_server_submit": [_vp, _P(SimRequest), _P(_i64)],
+    "sim_server_wait": [_vp, _i64, _i32, _P(ctypes.c_double)],
+    "sim_server_cancel": [_vp, _i64],
+    "sim_server_stats_get": [_vp, _P(ServerStats)],
+    "sim_server_destroy": [_vp],
     "sim_get_render_config": [_vp, _P(RenderConfig)],
     "sim_set_render_config": [_vp, _P(RenderConfig)],
     "sim_autotune_render": [_vp, _i32, _vp, _vp, _vp, _vp, _i32, _P(RenderConfig), _P(ctypes.c_float), _i32, _vp],

@@ -58,7 +58,8 @@ struct sim_ctx {
     CamConsts cam{};
     size_t budget = 0;
     size_t used = 0;
-    std::mutex mu;
+    std::mutex mu;        // scene table
+    std::mutex alloc_mu;  // budget accounting
     std::vector<SceneRec> scenes;
     SceneRow* d_table = nullptr;
     int table_cap = 0;
@@ -92,6 +93,7 @@ struct DeviceGuard {
 int ctx_alloc(sim_ctx* c, size_t bytes, void** out) {
     *out = nullptr;
     if (bytes == 0) bytes = 16;
+    std::lock_guard<std::mutex> lk(c->alloc_mu);
     if (c->budget && c->used + bytes > c->budget)
         return fail(SIM_ERR_BUDGET, "memory budget exceeded: need " + std::to_string(bytes) + " B, used " +
                                         std::to_string(c->used) + " of " + std::to_string(c->budget));
@@ -108,6 +110,7 @@ void ctx_free(sim_ctx* c, void* p, size_t bytes) {
     if (!p) return;
     cudaFree(p);
     if (bytes == 0) bytes = 16;
+    std::lock_guard<std::mutex> lk(c->alloc_mu);
     c->used -= bytes;
 }
 
@@ -241,6 +244,7 @@ int upload_table(sim_ctx* c) {
 }
 
 int max_scene_depth(const sim_ctx* c) {
+    std::lock_guard<std::mutex> lk(const_cast<sim_ctx*>(c)->mu);
     int d = 0;
     for (const auto& s : c->scenes)
         if (s.live) d = std::max(d, s.r.depth);
@@ -286,6 +290,7 @@ void free_scene(sim_ctx* c, SceneRec& s) {
 
 RenderArgs render_args(sim_ctx* c, int n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb,
                        int32_t* hit) {
+    std::lock_guard<std::mutex> lk(c->mu);  // scene table pointer and size
     RenderArgs a;
     a.n_agents = n;
     a.scene_of_agent = soa;
@@ -910,5 +915,31 @@ int render_scene_with_scratch(sim_ctx* c, int n, int scene_id, const int32_t* so
     cudaError_t e = launch_render(a, c->rcfg, ctas, false, s);
     return e == cudaSuccess ? SIM_OK : cuda_fail(e, "ray-cast launch");
 }
+
+}  // namespace vf
+
+namespace vf {
+
+int ctx_alloc_ext(sim_ctx* c, size_t bytes, void** out) { return ctx_alloc(c, bytes, out); }
+void ctx_free_ext(sim_ctx* c, void* p, size_t bytes) { ctx_free(c, p, bytes); }
+void ctx_image_size(const sim_ctx* c, int* W, int* H) {
+    *W = c->cam.W;
+    *H = c->cam.H;
+}
+bool ctx_scene_live(sim_ctx* c, int scene_id) {
+    std::lock_guard<std::mutex> lk(c->mu);
+    return scene_id >= 0 && scene_id < (int)c->scenes.size() && c->scenes[scene_id].live;
+}
+int ctx_step(sim_ctx* c, int n, float* state, const float* cmd, cudaStream_t s) {
+    cudaError_t e = launch_step(c->dyn, n, state, cmd, nullptr, s);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e, "step launch");
+}
+int ctx_render_own(sim_ctx* c, int n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb,
+                   unsigned* counters, cudaStream_t s) {
+    int rc = check_render_args(c, n, soa, state);
+    if (rc) return rc;
+    return do_render(c, n, soa, state, depth, rgb, nullptr, false, c->rcfg, s, counters);
+}
+int ctx_fail(int code, const char* msg) { return fail(code, msg); }
 
 }  // namespace vf

@@ -57,6 +57,15 @@ void set_last_error(const char* msg);
 int ctx_device(const sim_ctx* c);
 int render_scene_with_scratch(sim_ctx* c, int n, int scene_id, const int32_t* soa_dev, unsigned* counters_dev,
                               const float* state, float* depth, uint8_t* rgb, int32_t* hit, cudaStream_t s);
+// api.cu: context services for the step server.
+int ctx_alloc_ext(sim_ctx* c, size_t bytes, void** out);
+void ctx_free_ext(sim_ctx* c, void* p, size_t bytes);
+void ctx_image_size(const sim_ctx* c, int* W, int* H);
+bool ctx_scene_live(sim_ctx* c, int scene_id);
+int ctx_step(sim_ctx* c, int n, float* state, const float* cmd, cudaStream_t s);
+int ctx_render_own(sim_ctx* c, int n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb,
+                   unsigned* counters, cudaStream_t s);
+int ctx_fail(int code, const char* msg);
 // api.cu: launches a raycast kernel instance with the persistent grid size.
 cudaError_t launch_cfg(const void* kernel, const RenderArgs& a, int warps_per_cta, int ctas, size_t smem,
                        cudaStream_t s);
