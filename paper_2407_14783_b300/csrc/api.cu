@@ -48,6 +48,8 @@ struct sim_loop {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     unsigned* counters = nullptr;
+    void* sched_mem = nullptr;
+    int sched_cap = 0;
 };
 
 struct sim_ctx {
@@ -66,6 +68,11 @@ struct sim_ctx {
     int* d_err = nullptr;
     unsigned* d_ring = nullptr;  // [kRing][2]
     std::atomic<unsigned> ring_next{0};
+    std::atomic<unsigned> launch_id{0};
+    // longest-first scheduling hints shared by sim_render calls (see SchedBuf)
+    void* sched_mem = nullptr;
+    size_t sched_bytes = 0;
+    int sched_cap = 0;
     long long* d_stats = nullptr;
     sim_render_config rcfg{8, 4, 1, 0, 64, 4, 0, 0};  // fastest measured on the large scene
     // staging for sim_env_step
@@ -303,7 +310,12 @@ RenderArgs render_args(sim_ctx* c, int n, const int32_t* soa, const float* state
     a.cam = c->cam;
     const unsigned slot = c->ring_next.fetch_add(1) % kRing;
     a.counter = c->d_ring + 2 * slot;
-    a.done = c->d_ring + 2 * slot + 1;
+    a.done_ctas = c->d_ring + 2 * slot + 1;
+    a.sched = nullptr;
+    a.heavy = nullptr;
+    a.done = nullptr;
+    a.sched_cap = 0;
+    a.launch_id = c->launch_id.fetch_add(1) + 1;
     a.err = c->d_err;
     a.counters = c->d_stats;
     return a;
@@ -320,14 +332,59 @@ int check_render_args(sim_ctx* c, int n, const void* soa, const void* state) {
     return SIM_OK;
 }
 
+// Scheduling hints: 8 header words, two heavy-item lists of cap entries and one
+// mark per item (see RenderArgs).  Zeroed at allocation.
+size_t sched_bytes_for(int cap) { return 64 + 2 * sizeof(unsigned) * (size_t)cap + sizeof(unsigned long long) * cap; }
+
+int sched_alloc(sim_ctx* c, int cap, void** mem, cudaStream_t s) {
+    int rc = ctx_alloc(c, sched_bytes_for(cap), mem);
+    if (rc) return rc;
+    cudaError_t e = cudaMemsetAsync(*mem, 0, sched_bytes_for(cap), s);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e, "schedule reset");
+}
+
+void sched_attach(RenderArgs& a, void* mem, int cap) {
+    char* p = (char*)mem;
+    a.sched = (unsigned long long*)p;
+    a.heavy = (unsigned*)(p + 64);
+    a.done = (unsigned long long*)(p + 64 + 2 * sizeof(unsigned) * (size_t)cap);
+    a.sched_cap = cap;
+}
+
+// The context's shared hint buffer, grown (and reset) when a launch has more
+// work items than it holds.
+int ctx_sched(sim_ctx* c, long long items, cudaStream_t s) {
+    if (items <= c->sched_cap) return SIM_OK;
+    int cap = 1 << 16;
+    while (cap < items) cap <<= 1;
+    void* mem;
+    int rc = sched_alloc(c, cap, &mem, s);
+    if (rc) return rc;
+    if (c->sched_mem) {
+        cudaStreamSynchronize(s);
+        ctx_free(c, c->sched_mem, c->sched_bytes);
+    }
+    c->sched_mem = mem;
+    c->sched_bytes = sched_bytes_for(cap);
+    c->sched_cap = cap;
+    return SIM_OK;
+}
+
+long long render_items(const sim_ctx* c, int n, const sim_render_config& cfg) {
+    const long long tx = (c->cam.W + cfg.tile_w - 1) / cfg.tile_w, ty = (c->cam.H + cfg.tile_h - 1) / cfg.tile_h;
+    return (long long)n * tx * ty;
+}
+
 int do_render(sim_ctx* c, int n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb, int32_t* hit,
-              bool count, const sim_render_config& cfg, cudaStream_t s, unsigned* own_counters = nullptr) {
+              bool count, const sim_render_config& cfg, cudaStream_t s, unsigned* own_counters = nullptr,
+              void* sched_mem = nullptr, int sched_cap = 0) {
     if (n == 0) return SIM_OK;
     RenderArgs a = render_args(c, n, soa, state, depth, rgb, hit);
     if (own_counters) {
         a.counter = own_counters;
-        a.done = own_counters + 1;
+        a.done_ctas = own_counters + 1;
     }
+    if (sched_mem) sched_attach(a, sched_mem, sched_cap);
     int ctas = 0;
     if (cfg.ctas_per_sm > 0) ctas = cfg.ctas_per_sm * c->num_sms;
     cudaError_t e = launch_render(a, cfg, ctas, count, s);
@@ -416,6 +473,7 @@ int sim_destroy_ctx(sim_ctx* c) {
     ctx_free(c, c->d_err, sizeof(int));
     ctx_free(c, c->d_ring, sizeof(unsigned) * 2 * kRing);
     ctx_free(c, c->d_stats, sizeof(long long) * 8);
+    if (c->sched_mem) ctx_free(c, c->sched_mem, c->sched_bytes);
     ctx_free(c, c->d_cmd, 0);
     ctx_free(c, c->d_depth, 0);
     ctx_free(c, c->d_rgb, 0);
@@ -585,7 +643,10 @@ int sim_render(sim_ctx* c, int32_t n, const int32_t* soa, const float* state, fl
     int rc = check_render_args(c, n, soa, state);
     if (rc) return rc;
     DeviceGuard g(c->device);
-    return do_render(c, n, soa, state, depth, rgb, hit, false, c->rcfg, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    const sim_render_config cfg = c->rcfg;
+    if ((rc = ctx_sched(c, render_items(c, n, cfg), s))) return rc;
+    return do_render(c, n, soa, state, depth, rgb, hit, false, cfg, s, nullptr, c->sched_mem, c->sched_cap);
 }
 
 int sim_render_counted(sim_ctx* c, int32_t n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb,
@@ -704,6 +765,12 @@ int sim_loop_create(sim_ctx* c, sim_loop** out, int32_t n, int32_t T, const int3
     }
     L->counters = (unsigned*)cnt;
     cudaStream_t s = (cudaStream_t)stream;
+    L->sched_cap = (int)std::max<long long>(1, render_items(c, n, c->rcfg));
+    if ((rc = sched_alloc(c, L->sched_cap, &L->sched_mem, s))) {
+        ctx_free(c, L->counters, 2 * sizeof(unsigned));
+        delete L;
+        return rc;
+    }
     cudaStream_t cap;
     cudaError_t e = cudaMemsetAsync(L->counters, 0, 2 * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -720,7 +787,7 @@ int sim_loop_create(sim_ctx* c, sim_loop** out, int32_t n, int32_t T, const int3
         if (e != cudaSuccess) break;
         const size_t slot = (size_t)(t % n_frames);
         rc = do_render(c, n, soa, state, depth ? depth + slot * frame : nullptr, rgb ? rgb + slot * frame * 3 : nullptr,
-                       nullptr, false, c->rcfg, cap, L->counters);
+                       nullptr, false, c->rcfg, cap, L->counters, L->sched_mem, L->sched_cap);
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
@@ -750,6 +817,7 @@ int sim_loop_destroy(sim_loop* L) {
     if (L->exec) cudaGraphExecDestroy(L->exec);
     if (L->graph) cudaGraphDestroy(L->graph);
     ctx_free(L->ctx, L->counters, 2 * sizeof(unsigned));
+    if (L->sched_mem) ctx_free(L->ctx, L->sched_mem, sched_bytes_for(L->sched_cap));
     delete L;
     return SIM_OK;
 }
@@ -910,7 +978,7 @@ int render_scene_with_scratch(sim_ctx* c, int n, int scene_id, const int32_t* so
     DeviceGuard g(c->device);
     RenderArgs a = render_args(c, n, soa_dev, state, depth, rgb, hit);
     a.counter = counters_dev;
-    a.done = counters_dev + 1;
+    a.done_ctas = counters_dev + 1;
     int ctas = c->rcfg.ctas_per_sm > 0 ? c->rcfg.ctas_per_sm * c->num_sms : 0;
     cudaError_t e = launch_render(a, c->rcfg, ctas, false, s);
     return e == cudaSuccess ? SIM_OK : cuda_fail(e, "ray-cast launch");

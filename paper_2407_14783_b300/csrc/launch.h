@@ -44,9 +44,18 @@ struct RenderArgs {
     int n_scenes;
     CamConsts cam;
     unsigned* counter;   // work-item counter (zero between launches)
-    unsigned* done;      // finished-CTA counter (zero between launches)
+    unsigned* done_ctas; // finished-CTA counter (zero between launches)
     int* err;
     long long* counters; // traversal counters (COUNT builds)
+    // Longest-first scheduling state carried between launches (may be null):
+    // sched[0..1] cost sums, sched[2..3] heavy-list lengths, sched[4] epoch,
+    // sched[5] item count of the launch that wrote the lists; heavy[2][cap]
+    // item lists; done[cap] marks of items already rendered in this launch.
+    unsigned long long* sched;
+    unsigned* heavy;
+    unsigned long long* done;
+    int sched_cap;
+    unsigned launch_id;  // distinct per host-side launch
 };
 size_t render_smem_bytes(int warps_per_cta, int stack_depth, int rpl);
 int render_config_list(sim_render_config* out, int max);

@@ -125,16 +125,50 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_k
     // COUNT statistics: per work item (warp) and per ray (what each ray's own walk needs)
     long long c_nodes = 0, c_tris = 0, c_large = 0, c_items = 0, c_need_nodes = 0, c_need_tris = 0;
 
+    // Longest-first order: tiles that cost more than twice the mean in the
+    // previous launch (same item count) are handed out first, then all others.
+    const bool sched = A.sched != nullptr && total <= A.sched_cap;
+    unsigned long long mark = 0;
+    unsigned n_heavy = 0;
+    float thr = 0.0f;
+    int rd = 0;
+    if (sched) {
+        const unsigned ep = (unsigned)A.sched[4];
+        rd = ep & 1;
+        mark = ((unsigned long long)A.launch_id << 32) | ep;
+        if ((long long)A.sched[5] == total) {
+            n_heavy = (unsigned)min((unsigned long long)total, A.sched[2 + rd]);
+            thr = 2.0f * (float)A.sched[rd] / (float)total;
+        }
+    }
     for (;;) {
         long long item = 0;
-        if (lane == 0) item = (long long)atomicAdd(A.counter, 1u);
+        if (lane == 0) {
+            const long long k = (long long)atomicAdd(A.counter, 1u);
+            if (k < (long long)n_heavy) {
+                item = A.heavy[(size_t)rd * A.sched_cap + k];
+                // an entry from a concurrent launch of another size may not fit this one
+                if (item < total) __stcg(A.done + item, mark);
+                else item = -1;
+            } else {
+                item = k - n_heavy;
+                if (sched && item < total && __ldcg(A.done + item) == mark) item = -1;  // done in the first pass
+            }
+        }
         item = __shfl_sync(kFull, item, 0);
+        if (item < 0) continue;
         if (item >= total) break;
         // after a device-detected fault every warp stops taking work
         if (__shfl_sync(kFull, lane == 0 ? *(volatile int*)A.err : 0, 0) == kDevErrTraversal) break;
-        const int agent = (int)(item / tiles);
-        const int tile = (int)(item - (long long)agent * tiles);
-        const int tx0 = (tile % tiles_x) * TW, ty0 = (tile / tiles_x) * TH;
+        // Items run tile position by tile position across all agents, tile rows
+        // from the image centre outwards: rows near the horizon (long rays through
+        // clutter) are the costly ones and start first, floor and ceiling rows are
+        // cheap and fill the tail of the launch.
+        const int rank = (int)(item / A.n_agents);
+        const int agent = (int)(item - (long long)rank * A.n_agents);
+        const int rrow = rank / tiles_x, mid = tiles_y >> 1;
+        const int ty = (rrow & 1) ? mid - 1 - (rrow >> 1) : mid + (rrow >> 1);
+        const int tx0 = (rank % tiles_x) * TW, ty0 = ty * TH;
         const int sid = __ldg(A.scene_of_agent + agent);
         const bool scene_ok = sid >= 0 && sid < A.n_scenes && A.table[sid].live;
         if (!scene_ok && lane == 0) set_error(A.err, kDevErrNotFound);
@@ -193,6 +227,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_k
             ry.best_id = -1;
         }
 
+        int item_cost = 0;
         if (scene_ok) {
             // large triangles: cull against the tile's ray-segment bounds, test the rest
             if (row.n_large > 0) {
@@ -239,7 +274,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_k
                 need[q] = ray[q].live;
                 needmask[q] = 0ull;
             }
-            int iters = 0;
+            int& iters = item_cost;
             while (cur != kEmptyRoot) {
                 if (++iters > kIterCap) {
                     if (lane == 0) set_error(A.err, kDevErrTraversal);
@@ -388,6 +423,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_k
             __syncwarp();
         }
         if (COUNT) ++c_items;
+        if (sched && lane == 0) {
+            const int wr = rd ^ 1;
+            atomicAdd(&A.sched[wr], (unsigned long long)item_cost);
+            if (thr > 0.0f && (float)item_cost > thr) {
+                const unsigned long long k = atomicAdd(&A.sched[2 + wr], 1ull);
+                if (k < (unsigned long long)A.sched_cap) A.heavy[(size_t)wr * A.sched_cap + k] = (unsigned)item;
+            }
+        }
     }
 
     if (COUNT) {
@@ -411,9 +454,16 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_k
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(A.done, 1u) == gridDim.x - 1) {
+        if (atomicAdd(A.done_ctas, 1u) == gridDim.x - 1) {
             *A.counter = 0u;
-            *A.done = 0u;
+            *A.done_ctas = 0u;
+            if (sched) {
+                // this launch's read slot becomes the next launch's write slot
+                A.sched[rd] = 0ull;
+                A.sched[2 + rd] = 0ull;
+                A.sched[5] = (unsigned long long)total;
+                A.sched[4] = A.sched[4] + 1ull;
+            }
             __threadfence();
         }
     }

@@ -140,3 +140,26 @@ def test_unknown_scene_is_reported(make_sim, wl):
     assert sim.status() == -4          # SIM_ERR_NOT_FOUND, read and cleared
     assert sim.status() == 0
     assert torch.all(h[1] == -1) and torch.all(h[0] >= 0)
+
+
+def test_scheduling_hints_do_not_change_images(make_sim, wl):
+    """Renders after the first reorder work from the previous launch's tile costs;
+    images must equal a fresh context's, also when the agent count changes."""
+    from paper_2407_14783_b300.sim import to_soa
+    p = wl.params()
+    sc = wl.cluttered_scene(n_objects=800, size=(25.0, 25.0, 6.0), seed=9)
+    a = make_sim(p)
+    sa = a.add_workload_scene(sc)
+    s = wl.spawn_states(sc, 96, 17, 1100.0).astype(np.float32)
+    outs = [_render(a, sa, s) for _ in range(4)]          # launches 2.. use hints
+    small = _render(a, sa, s[:40])                          # different item count
+    again = _render(a, sa, s)
+    b = make_sim(p)
+    sb = b.add_workload_scene(sc)
+    fresh = _render(b, sb, s)
+    fresh_small = _render(b, sb, s[:40])
+    for o in outs + [again]:
+        for x, y in zip(o, fresh):
+            assert np.array_equal(x, y)
+    for x, y in zip(small, fresh_small):
+        assert np.array_equal(x, y)

@@ -133,6 +133,9 @@ def test_memory_admission(make_sim, wl):
     from paper_2407_14783_b300.serve import Server
     p, sim0, scenes, sids = _setup(make_sim, wl)
     srv0 = Server(sim0, capacity=512)
+    w_h, u_h = _hover(p)
+    s0, cm = _request(wl, scenes[1], 4, 1, 1, u_h, w_h)
+    _alone(sim0, sids[1], s0, cm, "last")      # the context's render-scheduling hints count too
     base = sim0.mem_usage()[0]
     srv0.close()
     n, T = 100, 6
