@@ -329,6 +329,17 @@ def run_ours(args):
     roof = raycast_roofline(sim, cnt, n, p, render_ms)
     clocks = clk.summary()
 
+    # nearest-obstacle query (the paper's obstacle-distance module) on the same agents
+    for _ in range(3):
+        sim.nearest_obstacle(ids, state, 10.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        sim.nearest_obstacle(ids, state, 10.0)
+    e1.record()
+    torch.cuda.synchronize()
+    near_ms = e0.elapsed_time(e1) / 20
+
     line = {"metric": METRIC, "value": value, "unit": "agent-frames/s", "n_gpus": ws, "steps": K, "warmup": W,
             "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic (procedural scene, seeded spawns and commands)",
@@ -339,6 +350,7 @@ def run_ours(args):
             "e2e": e2e, "gpu_launches": 2 * K,
             "breakdown_ms": {"dynamics": statistics.mean(dyn_ms), "render": render_ms},
             "roofline": roof,
+            "extras": {"nearest_obstacle": {"agents": n, "ms": near_ms, "queries_per_s": n / (near_ms * 1e-3)}},
             "clocks": clocks}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg(p, scene, w_h, u_h)

@@ -161,6 +161,54 @@ int sim_render_scene(sim_ctx* ctx, int32_t n_agents, int32_t scene_id, const flo
 int sim_render_scene_static(sim_ctx* ctx, int32_t n_agents, int32_t scene_id, const float* state, float* depth,
                             uint8_t* rgb, int32_t* hit_id, void* stream);
 
+/* Nearest obstacle (Sec. III-B: the obstacle-distance module that reports the
+ * nearest point of the obstacles without a collision happening): for every
+ * agent, the closest point of its scene's mesh to the agent's position.
+ *   scene_of_agent dev int32 [n]; state dev [17][n] (rows 0-2 used);
+ *   dist dev float32 [n]: distance, or max_dist when nothing is closer;
+ *   point dev float32 [3][n] or NULL: the closest point (the agent's position
+ *   when nothing is within max_dist); tri dev int32 [n] or NULL: its triangle
+ *   (lowest id among equal distances, -1 when nothing is within max_dist). */
+int sim_nearest_obstacle(sim_ctx* ctx, int32_t n_agents, const int32_t* scene_of_agent, const float* state,
+                         float max_dist, float* dist, float* point, int32_t* tri, void* stream);
+
+/* As sim_render, with a segmentation image as well: seg dev int32 [n][H][W]
+ * (or NULL) receives the hit triangle's label (sim_scene_set_labels; the
+ * triangle id when the scene has none) and -1 on a miss (the segmentation
+ * sensor of Sec. III-B, Fig. 3). */
+int sim_render_ex(sim_ctx* ctx, int32_t n_agents, const int32_t* scene_of_agent, const float* state, float* depth,
+                  uint8_t* rgb, int32_t* hit_id, int32_t* seg, void* stream);
+
+/* Per-triangle segmentation labels of a scene (host int32 [n_tris], e.g. object
+ * ids), or labels = NULL to drop them.  Synchronises the device. */
+int sim_scene_set_labels(sim_ctx* ctx, int32_t scene_id, const int32_t* labels, int64_t n_tris);
+
+/* Sensor noise of every later render on this context (domain randomisation of
+ * the vision sensors, Sec. III-D, Table II), or cfg = NULL for clean images.
+ * Per pixel, in this order: shot noise (Gaussian form: x' = (L + sqrt(L) z) / k
+ * with L = k x, k = *_shot, skipped when 0), additive Gaussian (sigma *_gauss),
+ * speckle (x' = x (1 + sigma z), sigma *_speckle), salt and pepper (probability
+ * *_salt_pepper, then 0 or the maximum with equal chance), clamp to [0, max]
+ * (max = max_depth for depth, 255 for colour, rounded to nearest even).  The
+ * segmentation image loses a pixel's label (-1) with probability seg_dropout.
+ * Hit ids are never noisy.  Draws come from SplitMix64 (Steele, Lea, Flood
+ * 2014) as output number i of the stream `seed`, with
+ * i = ((frame * n_agents + agent) * H * W + pixel) * 32 + slot (mod 2^64); slots:
+ * depth 0-7, colour channel c 8+8c..15+8c, segmentation 30; within a block of 8:
+ * Gaussian 0-1, speckle 2-3, shot 4-5, salt and pepper 6-7 (decision, value).
+ * A standard normal from slots (s, s+1): sqrt(-2 ln u1) cos(2 pi u2) with
+ * u1 = (x1 >> 40 + 0.5) / 2^24 and u2 = (x2 >> 40) / 2^24; a uniform for a decision
+ * is (x >> 40) / 2^24.  `frame` starts at first_frame and advances by one with
+ * every render launch.  Synchronises the device. */
+typedef struct sim_noise {
+    uint64_t seed;
+    uint64_t first_frame;
+    float depth_gauss, depth_speckle, depth_shot, depth_salt_pepper;
+    float rgb_gauss, rgb_speckle, rgb_shot, rgb_salt_pepper;
+    float seg_dropout;
+} sim_noise;
+int sim_set_noise(sim_ctx* ctx, const sim_noise* cfg);
+
 /* Reverse-mode derivative of one sim_step (the dynamics are differentiable,
  * Sec. III-A): given the pre-step state, the command and the cotangent of the
  * post-step state, write the cotangents of the pre-step state and the command.

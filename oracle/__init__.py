@@ -85,6 +85,8 @@ def lib():
             L.oracle_validate.argtypes = [vp, P(OracleParams), i64, dp, i64, P(ctypes.c_int64),
                                           P(ctypes.c_int32), P(ctypes.c_float), P(ctypes.c_uint8)]
             L.oracle_num_threads.restype = ctypes.c_int
+            L.oracle_nearest.argtypes = [vp, i64, dp, ctypes.c_double, dp, dp, P(ctypes.c_int32)]
+            L.oracle_point_triangle.argtypes = [vp, i64, dp, P(ctypes.c_int32), dp]
             _lib = L
         return _lib
 
@@ -203,6 +205,29 @@ class Scene:
         if rc:
             raise ValueError(f"oracle_render failed ({rc})")
         return {"depth": depth, "rgb": rgb, "id": hid, "tie": tie.astype(bool)}
+
+    def nearest(self, positions: np.ndarray, max_dist: float):
+        """Closest mesh point of every query point: (dist [n], point [n,3], tri [n])."""
+        pos = _f64(positions).reshape(-1, 3)
+        n = pos.shape[0]
+        dist = np.empty(n)
+        point = np.empty((n, 3))
+        tri = np.empty(n, np.int32)
+        rc = lib().oracle_nearest(self.handle, n, _ptr(pos, ctypes.c_double), float(max_dist),
+                                  _ptr(dist, ctypes.c_double), _ptr(point, ctypes.c_double),
+                                  _ptr(tri, ctypes.c_int32))
+        if rc:
+            raise ValueError(f"oracle_nearest failed ({rc})")
+        return dist, point, tri
+
+    def point_triangle(self, positions: np.ndarray, ids: np.ndarray) -> np.ndarray:
+        """Distance from each point to the given triangle (inf for an invalid id)."""
+        pos = _f64(positions).reshape(-1, 3)
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        out = np.empty(pos.shape[0])
+        lib().oracle_point_triangle(self.handle, pos.shape[0], _ptr(pos, ctypes.c_double),
+                                    _ptr(ids, ctypes.c_int32), _ptr(out, ctypes.c_double))
+        return out
 
     def validate(self, p: dict, states: np.ndarray, pix: np.ndarray, ids: np.ndarray, depth: np.ndarray):
         """Validity of claimed (id, depth) answers at flat pixel indices ``pix`` (see oracle.cpp)."""

@@ -743,6 +743,116 @@ int oracle_validate(const void* scene, const OracleParams* p, int64_t n, const d
     return 0;
 }
 
+// ------------------------------------------------------- nearest obstacle
+// Closest point of triangle (a, b, c) to point p, by the Voronoi regions of
+// the triangle: the three vertex regions, the three edge regions, and the
+// face region (projection onto the plane).  Barycentric-style parameters are
+// computed from dot products of the edge vectors with the point's offsets.
+static void closest_on_triangle(const double p[3], const double a[3], const double b[3], const double c[3],
+                                double out[3]) {
+    auto sub = [](const double* x, const double* y, double* r) {
+        for (int j = 0; j < 3; ++j) r[j] = x[j] - y[j];
+    };
+    auto dot = [](const double* x, const double* y) { return x[0] * y[0] + x[1] * y[1] + x[2] * y[2]; };
+    double ab[3], ac[3], ap[3], bp[3], cp[3];
+    sub(b, a, ab);
+    sub(c, a, ac);
+    sub(p, a, ap);
+    const double d1 = dot(ab, ap), d2 = dot(ac, ap);
+    if (d1 <= 0.0 && d2 <= 0.0) {  // vertex a
+        for (int j = 0; j < 3; ++j) out[j] = a[j];
+        return;
+    }
+    sub(p, b, bp);
+    const double d3 = dot(ab, bp), d4 = dot(ac, bp);
+    if (d3 >= 0.0 && d4 <= d3) {  // vertex b
+        for (int j = 0; j < 3; ++j) out[j] = b[j];
+        return;
+    }
+    const double vc = d1 * d4 - d3 * d2;
+    if (vc <= 0.0 && d1 >= 0.0 && d3 <= 0.0) {  // edge ab
+        const double v = d1 / (d1 - d3);
+        for (int j = 0; j < 3; ++j) out[j] = a[j] + v * ab[j];
+        return;
+    }
+    sub(p, c, cp);
+    const double d5 = dot(ab, cp), d6 = dot(ac, cp);
+    if (d6 >= 0.0 && d5 <= d6) {  // vertex c
+        for (int j = 0; j < 3; ++j) out[j] = c[j];
+        return;
+    }
+    const double vb = d5 * d2 - d1 * d6;
+    if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) {  // edge ac
+        const double w = d2 / (d2 - d6);
+        for (int j = 0; j < 3; ++j) out[j] = a[j] + w * ac[j];
+        return;
+    }
+    const double va = d3 * d6 - d5 * d4;
+    if (va <= 0.0 && (d4 - d3) >= 0.0 && (d5 - d6) >= 0.0) {  // edge bc
+        const double w = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+        for (int j = 0; j < 3; ++j) out[j] = b[j] + w * (c[j] - b[j]);
+        return;
+    }
+    const double den = 1.0 / (va + vb + vc);  // face
+    const double v = vb * den, w = vc * den;
+    for (int j = 0; j < 3; ++j) out[j] = a[j] + ab[j] * v + ac[j] * w;
+}
+
+// For every query point (positions [n][3]): the distance to the closest point
+// of the mesh (brute force over all triangles), that point, and the lowest id
+// among triangles within 1e-12 of the minimum; distances above max_dist give
+// max_dist, id -1 and the query point itself.
+int oracle_nearest(const void* scene, int64_t n, const double* pos, double max_dist, double* dist, double* point,
+                   int32_t* tri) {
+    const OracleScene* s = static_cast<const OracleScene*>(scene);
+    if (!s || n < 0) return -1;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t a = 0; a < n; ++a) {
+        const double* p = pos + 3 * a;
+        double best = std::numeric_limits<double>::infinity(), bp[3] = {p[0], p[1], p[2]};
+        int32_t bid = -1;
+        for (int32_t id = 0; id < (int32_t)s->tris.size(); ++id) {
+            const Tri& t = s->tris[id];
+            double q[3];
+            closest_on_triangle(p, t.v0, t.v1, t.v2, q);
+            const double d = std::sqrt((q[0] - p[0]) * (q[0] - p[0]) + (q[1] - p[1]) * (q[1] - p[1]) +
+                                       (q[2] - p[2]) * (q[2] - p[2]));
+            if (d < best - 1e-12 || (std::fabs(d - best) <= 1e-12 && id < bid)) {
+                best = d;
+                bid = id;
+                for (int j = 0; j < 3; ++j) bp[j] = q[j];
+            }
+        }
+        if (!(best <= max_dist)) {
+            best = max_dist;
+            bid = -1;
+            for (int j = 0; j < 3; ++j) bp[j] = p[j];
+        }
+        dist[a] = best;
+        tri[a] = bid;
+        for (int j = 0; j < 3; ++j) point[3 * a + j] = bp[j];
+    }
+    return 0;
+}
+
+// Distance from p to triangle id (for validating a claimed nearest triangle).
+int oracle_point_triangle(const void* scene, int64_t n, const double* pos, const int32_t* ids, double* dist) {
+    const OracleScene* s = static_cast<const OracleScene*>(scene);
+    if (!s || n < 0) return -1;
+    for (int64_t a = 0; a < n; ++a) {
+        if (ids[a] < 0 || ids[a] >= (int32_t)s->tris.size()) {
+            dist[a] = std::numeric_limits<double>::infinity();
+            continue;
+        }
+        const Tri& t = s->tris[ids[a]];
+        double q[3];
+        closest_on_triangle(pos + 3 * a, t.v0, t.v1, t.v2, q);
+        const double* p = pos + 3 * a;
+        dist[a] = std::sqrt((q[0] - p[0]) * (q[0] - p[0]) + (q[1] - p[1]) * (q[1] - p[1]) + (q[2] - p[2]) * (q[2] - p[2]));
+    }
+    return 0;
+}
+
 int oracle_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -59,6 +59,14 @@ class RenderCounters(ctypes.Structure):
                 ("need_tri_tests", ctypes.c_int64)]
 
 
+class SimNoise(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("first_frame", ctypes.c_uint64), ("depth_gauss", ctypes.c_float),
+                ("depth_speckle", ctypes.c_float), ("depth_shot", ctypes.c_float),
+                ("depth_salt_pepper", ctypes.c_float), ("rgb_gauss", ctypes.c_float),
+                ("rgb_speckle", ctypes.c_float), ("rgb_shot", ctypes.c_float), ("rgb_salt_pepper", ctypes.c_float),
+                ("seg_dropout", ctypes.c_float)]
+
+
 class SimRequest(ctypes.Structure):
     _fields_ = [("scene_id", ctypes.c_int32), ("n_agents", ctypes.c_int32), ("n_steps", ctypes.c_int32),
                 ("frames", ctypes.c_int32), ("state0", ctypes.c_void_p), ("cmds", ctypes.c_void_p),
@@ -98,8 +106,12 @@ SIGNATURES = {
     "sim_step": [_vp, _i32, _vp, _vp, _vp, _vp],
     "sim_render": [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
     "sim_render_scene": [_vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp],
+    "sim_render_ex": [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "sim_scene_set_labels": [_vp, _i32, _vp, _i64],
+    "sim_set_noise": [_vp, _vp],
     "sim_render_scene_static": [_vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp],
     "sim_step_backward": [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
+    "sim_nearest_obstacle": [_vp, _i32, _vp, _vp, ctypes.c_float, _vp, _vp, _vp, _vp],
     "sim_rollout": [_vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
     "sim_rollout_backward": [_vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
     "sim_env_step": [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp],

@@ -35,6 +35,7 @@ constexpr int kRing = 64;  // work-counter slots, so renders on different stream
 
 struct SceneRec {
     bool live = false;
+    int32_t* labels = nullptr;  // segmentation labels per triangle (owned), or null
     void* mem[4] = {nullptr, nullptr, nullptr, nullptr};
     size_t bytes = 0;
     int64_t n_tris = 0;
@@ -69,6 +70,8 @@ struct sim_ctx {
     unsigned* d_ring = nullptr;  // [kRing][2]
     std::atomic<unsigned> ring_next{0};
     std::atomic<unsigned> launch_id{0};
+    NoiseParams noise{};
+    unsigned long long* d_noise_frame = nullptr;
     // longest-first scheduling hints shared by sim_render calls (see SchedBuf)
     void* sched_mem = nullptr;
     size_t sched_bytes = 0;
@@ -239,6 +242,7 @@ int upload_table(sim_ctx* c) {
         r.tris = s.r.tris;
         r.large = s.r.large;
         r.colors = s.r.colors;
+        r.labels = s.labels;
         r.root = s.r.root;
         r.n_large = s.r.n_large;
         r.depth = s.r.depth;
@@ -285,6 +289,8 @@ cudaError_t scene_alloc(void* user, LbvhResult* r) {
 }
 
 void free_scene(sim_ctx* c, SceneRec& s) {
+    if (s.labels) ctx_free(c, s.labels, sizeof(int32_t) * (size_t)std::max<int64_t>(s.n_tris, 1));
+    s.labels = nullptr;
     const size_t sz[4] = {(size_t)s.r.n_nodes * 64, (size_t)s.r.n_bvh * 48, (size_t)s.r.n_large * 48,
                           (size_t)s.n_tris * 4};
     for (int i = 0; i < 4; ++i) {
@@ -316,6 +322,9 @@ RenderArgs render_args(sim_ctx* c, int n, const int32_t* soa, const float* state
     a.done = nullptr;
     a.sched_cap = 0;
     a.launch_id = c->launch_id.fetch_add(1) + 1;
+    a.seg = nullptr;
+    a.noise = c->noise;
+    a.noise_frame = c->d_noise_frame;
     a.err = c->d_err;
     a.counters = c->d_stats;
     return a;
@@ -377,9 +386,10 @@ long long render_items(const sim_ctx* c, int n, const sim_render_config& cfg) {
 
 int do_render(sim_ctx* c, int n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb, int32_t* hit,
               bool count, const sim_render_config& cfg, cudaStream_t s, unsigned* own_counters = nullptr,
-              void* sched_mem = nullptr, int sched_cap = 0) {
+              void* sched_mem = nullptr, int sched_cap = 0, int32_t* seg = nullptr) {
     if (n == 0) return SIM_OK;
     RenderArgs a = render_args(c, n, soa, state, depth, rgb, hit);
+    a.seg = seg;
     if (own_counters) {
         a.counter = own_counters;
         a.done_ctas = own_counters + 1;
@@ -442,12 +452,14 @@ int sim_create_ctx(sim_ctx** out, int device, const sim_params* p, size_t mem_bu
     c->params = *p;
     DeviceGuard g(device);
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-    void *err, *ring, *stats;
+    void *err, *ring, *stats, *nf;
     if ((rc = ctx_alloc(c, sizeof(int), &err)) || (rc = ctx_alloc(c, sizeof(unsigned) * 2 * kRing, &ring)) ||
-        (rc = ctx_alloc(c, sizeof(long long) * 8, &stats))) {
+        (rc = ctx_alloc(c, sizeof(long long) * 8, &stats)) || (rc = ctx_alloc(c, sizeof(unsigned long long), &nf))) {
         sim_destroy_ctx(c);
         return rc;
     }
+    c->d_noise_frame = (unsigned long long*)nf;
+    cudaMemset(c->d_noise_frame, 0, sizeof(unsigned long long));
     c->d_err = (int*)err;
     c->d_ring = (unsigned*)ring;
     c->d_stats = (long long*)stats;
@@ -473,6 +485,7 @@ int sim_destroy_ctx(sim_ctx* c) {
     ctx_free(c, c->d_err, sizeof(int));
     ctx_free(c, c->d_ring, sizeof(unsigned) * 2 * kRing);
     ctx_free(c, c->d_stats, sizeof(long long) * 8);
+    ctx_free(c, c->d_noise_frame, sizeof(unsigned long long));
     if (c->sched_mem) ctx_free(c, c->sched_mem, c->sched_bytes);
     ctx_free(c, c->d_cmd, 0);
     ctx_free(c, c->d_depth, 0);
@@ -638,15 +651,77 @@ int sim_rollout_backward(sim_ctx* c, int32_t n, int32_t T, int32_t K, const floa
     return e == cudaSuccess ? SIM_OK : cuda_fail(e, "sim_rollout_backward launch");
 }
 
-int sim_render(sim_ctx* c, int32_t n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb,
-               int32_t* hit, void* stream) {
+int sim_render_ex(sim_ctx* c, int32_t n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb,
+                  int32_t* hit, int32_t* seg, void* stream) {
     int rc = check_render_args(c, n, soa, state);
     if (rc) return rc;
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     const sim_render_config cfg = c->rcfg;
     if ((rc = ctx_sched(c, render_items(c, n, cfg), s))) return rc;
-    return do_render(c, n, soa, state, depth, rgb, hit, false, cfg, s, nullptr, c->sched_mem, c->sched_cap);
+    return do_render(c, n, soa, state, depth, rgb, hit, false, cfg, s, nullptr, c->sched_mem, c->sched_cap, seg);
+}
+
+int sim_render(sim_ctx* c, int32_t n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb,
+               int32_t* hit, void* stream) {
+    return sim_render_ex(c, n, soa, state, depth, rgb, hit, nullptr, stream);
+}
+
+int sim_set_noise(sim_ctx* c, const sim_noise* cfg) {
+    if (!c) return fail(SIM_ERR_INVALID_ARG, "null context");
+    NoiseParams np{};
+    unsigned long long frame = 0;
+    if (cfg) {
+        const float v[9] = {cfg->depth_gauss, cfg->depth_speckle, cfg->depth_shot, cfg->depth_salt_pepper,
+                            cfg->rgb_gauss,   cfg->rgb_speckle,   cfg->rgb_shot,   cfg->rgb_salt_pepper,
+                            cfg->seg_dropout};
+        for (float x : v)
+            if (!(x >= 0.0f) || !std::isfinite(x)) return fail(SIM_ERR_INVALID_ARG, "noise parameters must be >= 0");
+        if (cfg->depth_salt_pepper > 1 || cfg->rgb_salt_pepper > 1 || cfg->seg_dropout > 1)
+            return fail(SIM_ERR_INVALID_ARG, "probabilities must be <= 1");
+        np.enabled = 1;
+        np.seed = cfg->seed;
+        np.d_gauss = cfg->depth_gauss;
+        np.d_speckle = cfg->depth_speckle;
+        np.d_shot = cfg->depth_shot;
+        np.d_sp = cfg->depth_salt_pepper;
+        np.c_gauss = cfg->rgb_gauss;
+        np.c_speckle = cfg->rgb_speckle;
+        np.c_shot = cfg->rgb_shot;
+        np.c_sp = cfg->rgb_salt_pepper;
+        np.s_sp = cfg->seg_dropout;
+        frame = cfg->first_frame;
+    }
+    DeviceGuard g(c->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_noise_frame, &frame, sizeof(frame), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "noise set-up");
+    c->noise = np;
+    return SIM_OK;
+}
+
+int sim_scene_set_labels(sim_ctx* c, int32_t id, const int32_t* labels, int64_t n) {
+    if (!c) return fail(SIM_ERR_INVALID_ARG, "null context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (id < 0 || id >= (int)c->scenes.size() || !c->scenes[id].live) return fail(SIM_ERR_NOT_FOUND, "no such scene");
+    SceneRec& r = c->scenes[id];
+    if (labels && n != r.n_tris) return fail(SIM_ERR_INVALID_ARG, "need one label per triangle");
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    if (r.labels) ctx_free(c, r.labels, sizeof(int32_t) * (size_t)std::max<int64_t>(r.n_tris, 1));
+    r.labels = nullptr;
+    if (labels && n > 0) {
+        void* p;
+        int rc = ctx_alloc(c, sizeof(int32_t) * n, &p);
+        if (rc) return rc;
+        cudaError_t e = cudaMemcpy(p, labels, sizeof(int32_t) * n, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            ctx_free(c, p, sizeof(int32_t) * n);
+            return cuda_fail(e, "label upload");
+        }
+        r.labels = (int32_t*)p;
+    }
+    return upload_table(c);
 }
 
 int sim_render_counted(sim_ctx* c, int32_t n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb,
@@ -882,6 +957,30 @@ int sim_autotune_render(sim_ctx* c, int32_t n, const int32_t* soa, const float* 
     c->rcfg = cfgs[best_i];
     *best = cfgs[best_i];
     return SIM_OK;
+}
+
+int sim_nearest_obstacle(sim_ctx* c, int32_t n, const int32_t* soa, const float* state, float max_dist, float* dist,
+                         float* point, int32_t* tri, void* stream) {
+    if (!c || n < 0 || (n > 0 && (!soa || !state || !dist)) || !(max_dist > 0.0f))
+        return fail(SIM_ERR_INVALID_ARG, "bad sim_nearest_obstacle arguments");
+    if (n == 0) return SIM_OK;
+    DeviceGuard g(c->device);
+    NearestArgs a;
+    a.n = n;
+    a.scene_of_agent = soa;
+    a.state = state;
+    a.max_dist = max_dist;
+    a.dist = dist;
+    a.point = point;
+    a.tri = tri;
+    a.err = c->d_err;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        a.table = c->d_table;
+        a.n_scenes = (int)c->scenes.size();
+    }
+    cudaError_t e = launch_nearest(a, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e, "nearest-obstacle launch");
 }
 
 int sim_get_status(sim_ctx* c, void* stream, int32_t timeout_ms) {

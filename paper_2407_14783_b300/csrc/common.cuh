@@ -57,6 +57,7 @@ struct SceneRow {
     const float4* tris;      // 3 float4 per triangle, leaf order
     const float4* large;     // 3 float4 per large triangle (tested by every ray)
     const uint32_t* colors;  // RGB8 per original triangle id
+    const int32_t* labels;   // segmentation label per original triangle id (null: the id itself)
     int32_t root;
     int32_t n_large;
     int32_t depth;
@@ -73,5 +74,22 @@ __host__ __device__ inline void leaf_decode(int32_t code, int32_t& first, int32_
 }
 
 __device__ inline void set_error(int* err, int code) { atomicCAS(err, 0, code); }
+
+// Sensor noise of the rendered images (Table II models), drawn from the
+// counter-based SplitMix64 generator: output number i of the stream `seed`.
+struct NoiseParams {
+    int enabled;
+    unsigned long long seed;
+    float d_gauss, d_speckle, d_shot, d_sp;   // depth: additive N(0,s^2) m, multiplicative, shot scale, salt&pepper
+    float c_gauss, c_speckle, c_shot, c_sp;   // colour channels (0-255 units)
+    float s_sp;                               // segmentation: probability of an unlabelled pixel
+};
+
+__host__ __device__ inline unsigned long long splitmix64_at(unsigned long long seed, unsigned long long i) {
+    unsigned long long z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
 
 }  // namespace vf

@@ -56,6 +56,9 @@ struct RenderArgs {
     unsigned long long* done;
     int sched_cap;
     unsigned launch_id;  // distinct per host-side launch
+    int32_t* seg;        // segmentation image [n][H][W] or null
+    NoiseParams noise;
+    unsigned long long* noise_frame;  // frame counter of the noise streams (advanced by every noisy launch)
 };
 size_t render_smem_bytes(int warps_per_cta, int stack_depth, int rpl);
 int render_config_list(sim_render_config* out, int max);
@@ -66,6 +69,21 @@ void set_last_error(const char* msg);
 int ctx_device(const sim_ctx* c);
 int render_scene_with_scratch(sim_ctx* c, int n, int scene_id, const int32_t* soa_dev, unsigned* counters_dev,
                               const float* state, float* depth, uint8_t* rgb, int32_t* hit, cudaStream_t s);
+// nearest.cu
+struct NearestArgs {
+    int n;
+    const int* scene_of_agent;
+    const float* state;
+    float max_dist;
+    float* dist;
+    float* point;  // [3][n] or null
+    int* tri;      // [n] or null
+    const SceneRow* table;
+    int n_scenes;
+    int* err;
+};
+cudaError_t launch_nearest(const NearestArgs& a, cudaStream_t s);
+
 // api.cu: context services for the step server.
 int ctx_alloc_ext(sim_ctx* c, size_t bytes, void** out);
 void ctx_free_ext(sim_ctx* c, void* p, size_t bytes);

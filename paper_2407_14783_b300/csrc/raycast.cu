@@ -108,6 +108,33 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
+// Noise draws of one pixel: 32 consecutive outputs of the generator starting
+// at ((frame * n_agents + agent) * H * W + pixel) * 32 (mod 2^64).  Slots: depth
+// 0-7, colour channel c 8 + 8c .. 15 + 8c, segmentation 30.  Within a block of 8:
+// Gaussian 0-1, speckle 2-3, shot 4-5, salt & pepper 6-7.
+__device__ __forceinline__ float unit_open(unsigned long long x) {
+    return ((float)(x >> 40) + 0.5f) * (1.0f / 16777216.0f);
+}
+__device__ __forceinline__ float unit_half_open(unsigned long long x) { return (float)(x >> 40) * (1.0f / 16777216.0f); }
+__device__ __forceinline__ float gauss_at(unsigned long long seed, unsigned long long i) {
+    const float u1 = unit_open(splitmix64_at(seed, i)), u2 = unit_half_open(splitmix64_at(seed, i + 1));
+    return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+// shot (Gaussian form: mean k x, variance k x, scaled back), additive, speckle,
+// salt & pepper, then clamp to [0, hi]
+__device__ float noisy(float x, float hi, float gs, float sp, float shot, float sandp, unsigned long long seed,
+                       unsigned long long b) {
+    if (shot > 0.0f) {
+        const float lam = shot * x;
+        x = (lam + sqrtf(fmaxf(lam, 0.0f)) * gauss_at(seed, b + 4)) / shot;
+    }
+    if (gs > 0.0f) x += gs * gauss_at(seed, b);
+    if (sp > 0.0f) x *= 1.0f + sp * gauss_at(seed, b + 2);
+    if (sandp > 0.0f && unit_half_open(splitmix64_at(seed, b + 6)) < sandp)
+        x = unit_half_open(splitmix64_at(seed, b + 7)) < 0.5f ? 0.0f : hi;
+    return fminf(fmaxf(x, 0.0f), hi);
+}
+
 template <int TW, int TH, int RPL, bool SMEM_STACK, bool STAGE, bool COUNT>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_kernel(RenderArgs A) {
     static_assert(TW * TH == 32 * RPL, "tile must hold 32 * RPL pixels");
@@ -125,6 +152,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_k
     // COUNT statistics: per work item (warp) and per ray (what each ray's own walk needs)
     long long c_nodes = 0, c_tris = 0, c_large = 0, c_items = 0, c_need_nodes = 0, c_need_tris = 0;
 
+    const unsigned long long noise_frame = A.noise.enabled ? *A.noise_frame : 0ull;
     // Longest-first order: tiles that cost more than twice the mean in the
     // previous launch (same item count) are handed out first, then all others.
     const bool sched = A.sched != nullptr && total <= A.sched_cap;
@@ -385,14 +413,32 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_k
         for (int q = 0; q < RPL; ++q) {
             const bool in = pix_r[q] < H && pix_c[q] < W;
             const size_t off = frame + (size_t)pix_r[q] * W + pix_c[q];
-            if (in && A.depth) A.depth[off] = ray[q].best_t;
+            const NoiseParams& nz = A.noise;
+            const unsigned long long nb =
+                ((noise_frame * (unsigned long long)A.n_agents + agent) * (unsigned long long)(H * W) +
+                 (unsigned long long)(pix_r[q] * W + pix_c[q])) * 32ull;
+            if (in && A.depth) {
+                float dv = ray[q].best_t;
+                if (nz.enabled) dv = noisy(dv, A.cam.max_depth, nz.d_gauss, nz.d_speckle, nz.d_shot, nz.d_sp, nz.seed, nb);
+                A.depth[off] = dv;
+            }
             if (in && A.hit_id) A.hit_id[off] = ray[q].best_id;
+            if (in && A.seg) {
+                int lab = ray[q].best_id >= 0 ? (row.labels ? __ldg(row.labels + ray[q].best_id) : ray[q].best_id) : -1;
+                if (nz.enabled && nz.s_sp > 0.0f && unit_half_open(splitmix64_at(nz.seed, nb + 30)) < nz.s_sp) lab = -1;
+                A.seg[off] = lab;
+            }
             if (A.rgb) {
                 const uint32_t col = ray[q].best_id >= 0 ? __ldg(row.colors + ray[q].best_id) : 0u;
                 const int p = lane + 32 * q;
-                rgbstage[3 * p + 0] = (uint8_t)(col & 0xFF);
-                rgbstage[3 * p + 1] = (uint8_t)((col >> 8) & 0xFF);
-                rgbstage[3 * p + 2] = (uint8_t)((col >> 16) & 0xFF);
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    uint32_t v = (col >> (8 * ch)) & 0xFFu;
+                    if (nz.enabled)
+                        v = (uint32_t)rintf(noisy((float)v, 255.0f, nz.c_gauss, nz.c_speckle, nz.c_shot, nz.c_sp, nz.seed,
+                                                  nb + 8 + 8 * ch));
+                    rgbstage[3 * p + ch] = (uint8_t)v;
+                }
             }
         }
         if (A.rgb) {
@@ -457,6 +503,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_k
         if (atomicAdd(A.done_ctas, 1u) == gridDim.x - 1) {
             *A.counter = 0u;
             *A.done_ctas = 0u;
+            if (A.noise.enabled) *A.noise_frame = noise_frame + 1ull;
             if (sched) {
                 // this launch's read slot becomes the next launch's write slot
                 A.sched[rd] = 0ull;

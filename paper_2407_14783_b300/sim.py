@@ -174,6 +174,46 @@ class Sim:
         B.check(rc, "sim_render", self.h)
         return depth, rgb, hit
 
+    def nearest_obstacle(self, scene_of_agent, state, max_dist: float = 10.0, stream=None):
+        """Closest mesh point of every agent: (dist [n], point [3, n], tri [n])."""
+        n = state.shape[1]
+        _need(scene_of_agent, torch.int32, (n,), "scene_of_agent")
+        _need(state, torch.float32, (STATE_DIM, n), "state")
+        dist = torch.empty((n,), device=state.device)
+        point = torch.empty((3, n), device=state.device)
+        tri = torch.empty((n,), dtype=torch.int32, device=state.device)
+        rc = self.L.sim_nearest_obstacle(self.h, n, _ptr(scene_of_agent), _ptr(state), float(max_dist), _ptr(dist),
+                                         _ptr(point), _ptr(tri), _stream(stream))
+        B.check(rc, "sim_nearest_obstacle", self.h)
+        return dist, point, tri
+
+    def render_seg(self, scene_of_agent, state, depth=None, rgb=None, hit=None, seg=None, stream=None):
+        """Render with a segmentation image (labels of sim_scene_set_labels, -1 on a miss)."""
+        n = state.shape[1]
+        _need(scene_of_agent, torch.int32, (n,), "scene_of_agent")
+        _need(state, torch.float32, (STATE_DIM, n), "state")
+        _need(depth, torch.float32, (n, self.H, self.W), "depth")
+        _need(rgb, torch.uint8, (n, self.H, self.W, 3), "rgb")
+        _need(hit, torch.int32, (n, self.H, self.W), "hit")
+        _need(seg, torch.int32, (n, self.H, self.W), "seg")
+        rc = self.L.sim_render_ex(self.h, n, _ptr(scene_of_agent), _ptr(state), _ptr(depth), _ptr(rgb), _ptr(hit),
+                                  _ptr(seg), _stream(stream))
+        B.check(rc, "sim_render_ex", self.h)
+        return depth, rgb, hit, seg
+
+    def set_labels(self, sid: int, labels):
+        lab = np.ascontiguousarray(np.asarray(labels, np.int32))
+        B.check(self.L.sim_scene_set_labels(self.h, sid, lab.ctypes.data, lab.shape[0]), "sim_scene_set_labels",
+                self.h)
+
+    def set_noise(self, cfg: dict | None):
+        """cfg keys as in sim_noise (missing ones 0); None for clean images."""
+        if cfg is None:
+            B.check(self.L.sim_set_noise(self.h, None), "sim_set_noise", self.h)
+            return
+        nz = B.SimNoise(**{k: cfg.get(k, 0) for k, _ in B.SimNoise._fields_})
+        B.check(self.L.sim_set_noise(self.h, ctypes.byref(nz)), "sim_set_noise", self.h)
+
     def render_config(self) -> dict:
         c = B.RenderConfig()
         B.check(self.L.sim_get_render_config(self.h, ctypes.byref(c)), "sim_get_render_config", self.h)
