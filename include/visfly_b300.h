@@ -79,6 +79,17 @@ typedef struct sim_params {
     float fov_deg;       /* horizontal field of view; square pixels */
     float max_depth;     /* m; farther hits are misses */
     float cam_off[3];    /* camera origin in the body frame, m */
+    int32_t controller;  /* command interpretation (Sec. III-A):
+                          * 0 CTBR: u = (collective thrust, body rates), normalised to [-1, 1];
+                          * 1 SRT: u_i = rotor i's thrust, (u_i + 1) / 2 * f(omega_max);
+                          * 2 LV: u = (world velocity m/s, yaw rad), geometric control;
+                          * 3 PS: u = (world position m, yaw rad), geometric control.
+                          * LV / PS: desired force m (a_d + g z) with
+                          * a_d = -K_pos (x - x_d) - K_vel v (PS) or -K_vel (v - v_d) (LV),
+                          * thrust = its projection on body z, desired attitude from its
+                          * direction and the yaw, moment J (-K_att e_R - K_omega Omega) +
+                          * Omega x J Omega with e_R = vee(R_d^T R - R^T R_d) / 2. */
+    float K_pos[3], K_vel[3], K_att[3], K_omega[3];
 } sim_params;
 
 /* Create a context on CUDA device `device`.  The context owns scenes, BVHs, the
@@ -212,6 +223,7 @@ int sim_set_noise(sim_ctx* ctx, const sim_noise* cfg);
 /* Reverse-mode derivative of one sim_step (the dynamics are differentiable,
  * Sec. III-A): given the pre-step state, the command and the cotangent of the
  * post-step state, write the cotangents of the pre-step state and the command.
+ * Implemented for the CTBR and SRT controllers (INVALID_ARG for LV / PS).
  * Clamps in the controller pass the gradient inside their range (boundary
  * included) and block it outside.  All dev float32: state_in [17][n], cmd
  * [4][n], g_state_out [17][n] (read), g_state_in [17][n] and g_cmd [4][n]

@@ -45,7 +45,9 @@ class OracleParams(ctypes.Structure):
         ("rate_max", ctypes.c_double * 3), ("K_rate", ctypes.c_double * 3), ("g", ctypes.c_double),
         ("dt", ctypes.c_double), ("n_sub", ctypes.c_int32), ("integrator", ctypes.c_int32),
         ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("fov_deg", ctypes.c_double),
-        ("max_depth", ctypes.c_double), ("cam_off", ctypes.c_double * 3),
+        ("max_depth", ctypes.c_double), ("cam_off", ctypes.c_double * 3), ("controller", ctypes.c_int32),
+        ("K_pos", ctypes.c_double * 3), ("K_vel", ctypes.c_double * 3), ("K_att", ctypes.c_double * 3),
+        ("K_omega", ctypes.c_double * 3),
     ]
 
 

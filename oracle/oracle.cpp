@@ -60,6 +60,8 @@ struct OracleParams {
     double fov_deg;
     double max_depth;
     double cam_off[3];
+    int32_t controller;   // 0 CTBR, 1 SRT, 2 LV, 3 PS
+    double K_pos[3], K_vel[3], K_att[3], K_omega[3];
 };
 }
 
@@ -91,6 +93,10 @@ inline Dual s_sqrt(const Dual& x) {
     if (r == 0.0) return {0.0, x.d == 0.0 ? 0.0 : std::numeric_limits<double>::infinity()};
     return {r, x.d / (2.0 * r)};
 }
+inline double s_cos(double x) { return std::cos(x); }
+inline double s_sin(double x) { return std::sin(x); }
+inline Dual s_cos(const Dual& x) { return {std::cos(x.v), -std::sin(x.v) * x.d}; }
+inline Dual s_sin(const Dual& x) { return {std::sin(x.v), std::cos(x.v) * x.d}; }
 inline double s_abs(double x) { return std::fabs(x); }
 inline Dual s_abs(const Dual& x) { return x.v < 0.0 ? -x : x; }
 
@@ -174,12 +180,28 @@ void solve4(const double Ain[4][4], const S bin[4], S f[4]) {
     }
 }
 
+// Thrust allocation shared by the controllers: solve A f = (collective
+// thrust, body moment) for the four rotor thrusts, clamp each to the
+// reachable range and convert to desired rotor speeds.
+template <class S>
+void allocate(const OracleParams& p, const S rhs[4], S omega_des[4]) {
+    double A[4][4];
+    mixer_matrix(p, A);
+    S f[4];
+    solve4(A, rhs, f);
+    const double f_lo = rotor_thrust(p, p.omega_min);
+    const double f_hi = rotor_thrust(p, p.omega_max);
+    for (int i = 0; i < 4; ++i) {
+        const S fi = s_clamp(f[i], f_lo, f_hi);
+        omega_des[i] = s_clamp(rotor_speed_for_thrust(p, fi), p.omega_min, p.omega_max);
+    }
+}
+
 // Body-rate (CTBR) controller [Sec. III-A, controllers; Sec. IV: CTBR is the
 // action type of all examples].  u[0] in [-1, 1] maps to a mass-normalised
 // collective thrust (u0 + 1) / 2 * a_max; u[1..3] scale to desired body rates.
 // A proportional rate loop with gyroscopic feed-forward gives the desired
-// moment; the mixer inverse gives rotor thrusts, which are clamped to the
-// reachable range and converted to desired rotor speeds.
+// moment; the allocation gives desired rotor speeds.
 template <class S>
 void controller_ctbr(const OracleParams& p, const S Om[3], const S u[4], S omega_des[4]) {
     const S a = (u[0] + 1.0) * 0.5 * p.a_max;
@@ -193,15 +215,108 @@ void controller_ctbr(const OracleParams& p, const S Om[3], const S u[4], S omega
         const S om_des = u[j + 1] * p.rate_max[j];
         rhs[j + 1] = p.J[j] * p.K_rate[j] * (om_des - Om[j]) + gyro[j];
     }
-    double A[4][4];
-    mixer_matrix(p, A);
-    S f[4];
-    solve4(A, rhs, f);
+    allocate(p, rhs, omega_des);
+}
+
+// Single-rotor thrusts (SRT) [Sec. III-A]: u_i in [-1, 1] maps to rotor i's
+// thrust (u_i + 1) / 2 * f(omega_max), clamped, converted to a rotor speed.
+template <class S>
+void controller_srt(const OracleParams& p, const S u[4], S omega_des[4]) {
     const double f_lo = rotor_thrust(p, p.omega_min);
     const double f_hi = rotor_thrust(p, p.omega_max);
     for (int i = 0; i < 4; ++i) {
-        const S fi = s_clamp(f[i], f_lo, f_hi);
+        const S fi = s_clamp((u[i] + 1.0) * 0.5 * f_hi, f_lo, f_hi);
         omega_des[i] = s_clamp(rotor_speed_for_thrust(p, fi), p.omega_min, p.omega_max);
+    }
+}
+
+template <class S>
+void rotation_matrix(const S q[4], S R[3][3]);
+
+// Linear-velocity (LV) and position (PS) commands with yaw [Sec. III-A, after
+// the geometric controller of Lee et al. 2010], world z up:
+//   desired acceleration  a_d = -K_pos (x - x_d) - K_vel v           (PS)
+//                         a_d = -K_vel (v - v_d)                     (LV)
+//   desired force F_d = m (a_d + g z); collective thrust = F_d . (R z_B);
+//   desired attitude R_d = [b1 b2 b3]: b3 = F_d / |F_d| (z when |F_d| = 0),
+//   b2 = b3 x c1 / |b3 x c1| with c1 = (cos yaw_d, sin yaw_d, 0) (or
+//   (-sin, cos, 0) when b3 x c1 vanishes), b1 = b2 x b3;
+//   attitude error e_R = vee(R_d^T R - R^T R_d) / 2, rate error e_W = Omega;
+//   moment = J (-K_att e_R - K_omega e_W) + Omega x J Omega;
+// then the same allocation as CTBR.  u = (x_d or v_d, yaw_d) in m, m/s, rad.
+template <class S>
+void controller_geometric(const OracleParams& p, const S y[17], const S u[4], bool position, S omega_des[4]) {
+    const S* x = y;
+    const S* v = y + 3;
+    const S* Om = y + 10;
+    S R[3][3];
+    rotation_matrix(y + 6, R);
+    S F[3];
+    for (int j = 0; j < 3; ++j) {
+        const S acc = position ? (-p.K_pos[j] * (x[j] - u[j]) - p.K_vel[j] * v[j]) : (-p.K_vel[j] * (v[j] - u[j]));
+        F[j] = p.mass * acc;
+    }
+    F[2] = F[2] + p.mass * p.g;
+    const S f_coll = F[0] * R[0][2] + F[1] * R[1][2] + F[2] * R[2][2];
+    const S nF = s_sqrt(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
+    S b3[3];
+    if (val(nF) < 1e-9) {
+        b3[0] = S(0.0);
+        b3[1] = S(0.0);
+        b3[2] = S(1.0);
+    } else {
+        for (int j = 0; j < 3; ++j) b3[j] = F[j] / nF;
+    }
+    S c1[3] = {s_cos(u[3]), s_sin(u[3]), S(0.0)};
+    auto cross = [](const S a[3], const S b[3], S c[3]) {
+        c[0] = a[1] * b[2] - a[2] * b[1];
+        c[1] = a[2] * b[0] - a[0] * b[2];
+        c[2] = a[0] * b[1] - a[1] * b[0];
+    };
+    S b2[3];
+    cross(b3, c1, b2);
+    S n2 = s_sqrt(b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]);
+    if (val(n2) < 1e-6) {
+        S c1b[3] = {-s_sin(u[3]), s_cos(u[3]), S(0.0)};
+        cross(b3, c1b, b2);
+        n2 = s_sqrt(b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]);
+    }
+    for (int j = 0; j < 3; ++j) b2[j] = b2[j] / n2;
+    S b1[3];
+    cross(b2, b3, b1);
+    S Rd[3][3];
+    for (int i = 0; i < 3; ++i) {
+        Rd[i][0] = b1[i];
+        Rd[i][1] = b2[i];
+        Rd[i][2] = b3[i];
+    }
+    // M = Rd^T R - R^T Rd (skew-symmetric); e_R = vee(M) / 2
+    S M[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            S a(0.0), b(0.0);
+            for (int k = 0; k < 3; ++k) {
+                a = a + Rd[k][i] * R[k][j];
+                b = b + R[k][i] * Rd[k][j];
+            }
+            M[i][j] = a - b;
+        }
+    const S eR[3] = {0.5 * M[2][1], 0.5 * M[0][2], 0.5 * M[1][0]};
+    S JOm[3], gyro[3], rhs[4];
+    for (int j = 0; j < 3; ++j) JOm[j] = p.J[j] * Om[j];
+    cross(Om, JOm, gyro);
+    rhs[0] = f_coll;
+    for (int j = 0; j < 3; ++j) rhs[j + 1] = p.J[j] * (-p.K_att[j] * eR[j] - p.K_omega[j] * Om[j]) + gyro[j];
+    allocate(p, rhs, omega_des);
+}
+
+template <class S>
+void controller(const OracleParams& p, const S y[17], const S u[4], S omega_des[4]) {
+    switch (p.controller) {
+        case 1: controller_srt(p, u, omega_des); break;
+        case 2: controller_geometric(p, y, u, false, omega_des); break;
+        case 3: controller_geometric(p, y, u, true, omega_des); break;
+        default: controller_ctbr(p, y + 10, u, omega_des); break;
     }
 }
 
@@ -266,7 +381,7 @@ void step_agent(const OracleParams& p, S y[17], const S u[4]) {
     for (int i = 0; i < 4; ++i) rotor_arm(p, i, rx[i], ry[i]);
     for (int sub = 0; sub < p.n_sub; ++sub) {
         S omega_des[4];
-        controller_ctbr(p, y + 10, u, omega_des);
+        controller(p, y, u, omega_des);
         for (int i = 0; i < 4; ++i) y[13 + i] = omega_des[i] + (y[13 + i] - omega_des[i]) * decay;
         S Fz(0.0), eta[3] = {S(0.0), S(0.0), S(0.0)};
         for (int i = 0; i < 4; ++i) {

@@ -34,7 +34,9 @@ class SimParams(ctypes.Structure):
         ("a_max", ctypes.c_float), ("rate_max", ctypes.c_float * 3), ("K_rate", ctypes.c_float * 3),
         ("g", ctypes.c_float), ("dt", ctypes.c_float), ("n_sub", ctypes.c_int32), ("integrator", ctypes.c_int32),
         ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("fov_deg", ctypes.c_float),
-        ("max_depth", ctypes.c_float), ("cam_off", ctypes.c_float * 3),
+        ("max_depth", ctypes.c_float), ("cam_off", ctypes.c_float * 3), ("controller", ctypes.c_int32),
+        ("K_pos", ctypes.c_float * 3), ("K_vel", ctypes.c_float * 3), ("K_att", ctypes.c_float * 3),
+        ("K_omega", ctypes.c_float * 3),
     ]
 
 

@@ -132,7 +132,7 @@ int derive(const sim_params& p, DynConsts& d, CamConsts& cam) {
         p.n_sub < 1 || p.n_sub > kMaxSub || (p.integrator != 0 && p.integrator != 1) || p.width < 1 ||
         p.height < 1 || p.width > 1024 || p.height > 1024 || !(p.fov_deg > 0 && p.fov_deg < 180) ||
         !(p.max_depth > 0) || !(p.omega_max >= p.omega_min) || !(p.c_lag >= 0) || !finite3(p.cam_off) ||
-        (p.k[2] == 0 && p.k[1] == 0) || p.k[2] < 0 || p.k[1] < 0)
+        (p.k[2] == 0 && p.k[1] == 0) || p.k[2] < 0 || p.k[1] < 0 || p.controller < 0 || p.controller > 3)
         return fail(SIM_ERR_INVALID_ARG, "invalid sim_params");
     memset(&d, 0, sizeof(d));
     d.mass = p.mass;
@@ -190,6 +190,15 @@ int derive(const sim_params& p, DynConsts& d, CamConsts& cam) {
         d.dk[j] = p.k[j];
     }
     d.dhalf_a_max_m = 0.5 * (double)p.a_max * p.mass;
+    d.controller = p.controller;
+    d.dmass = p.mass;
+    d.dg = p.g;
+    for (int j = 0; j < 3; ++j) {
+        d.dKpos[j] = p.K_pos[j];
+        d.dKvel[j] = p.K_vel[j];
+        d.dKatt[j] = p.K_att[j];
+        d.dKom[j] = p.K_omega[j];
+    }
     d.domega_min = p.omega_min;
     d.domega_max = p.omega_max;
     d.k0 = p.k[0];
@@ -626,6 +635,7 @@ int sim_step_backward(sim_ctx* c, int32_t n, const float* state_in, const float*
                       float* g_in, float* g_cmd, void* stream) {
     if (!c || n < 0 || (n > 0 && (!state_in || !cmd || !g_out || !g_in || !g_cmd)))
         return fail(SIM_ERR_INVALID_ARG, "bad sim_step_backward arguments");
+    if (c->dyn.controller > 1) return fail(SIM_ERR_INVALID_ARG, "the adjoint covers the CTBR and SRT controllers");
     DeviceGuard g(c->device);
     cudaError_t e = launch_step_backward(c->dyn, n, state_in, cmd, g_out, g_in, g_cmd, (cudaStream_t)stream);
     return e == cudaSuccess ? SIM_OK : cuda_fail(e, "sim_step_backward launch");
@@ -645,6 +655,7 @@ int sim_rollout_backward(sim_ctx* c, int32_t n, int32_t T, int32_t K, const floa
     if (!c || n < 0 || T < 1 || K < 1 || K > kMaxCkptK ||
         (n > 0 && (!ckpt || !cmds || !g_states || !g_state0 || !g_cmds)))
         return fail(SIM_ERR_INVALID_ARG, "bad sim_rollout_backward arguments");
+    if (c->dyn.controller > 1) return fail(SIM_ERR_INVALID_ARG, "the adjoint covers the CTBR and SRT controllers");
     DeviceGuard g(c->device);
     cudaError_t e =
         launch_rollout_backward(c->dyn, n, T, K, ckpt, cmds, g_states, g_state0, g_cmds, (cudaStream_t)stream);

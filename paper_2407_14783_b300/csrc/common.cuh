@@ -34,6 +34,8 @@ struct DynConsts {
     // inverse of the thrust polynomial turns FP32 rounding of the mixer solve
     // (about 1e-6 N) into rotor-speed errors of order 1 rad/s.
     double dJ[3], dJK[3], drate_max[3], dhalf_a_max_m, dAinv[4][4], df_lo, df_hi, dk[3], domega_min, domega_max;
+    int controller;                 // 0 CTBR, 1 SRT, 2 LV, 3 PS
+    double dmass, dg, dKpos[3], dKvel[3], dKatt[3], dKom[3];
     float decay;                    // exp(-c h)
     float drag[3];                  // rho Cd s / 2
     float g;

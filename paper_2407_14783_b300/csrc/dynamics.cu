@@ -47,19 +47,11 @@ struct CtrlTape {
     bool in_w[4];     // rotor speed inside [omega_min, omega_max]
 };
 
-// CTBR: u0 -> collective thrust m a, u1..3 -> desired rates; P rate loop with
-// gyroscopic feed-forward -> desired moment; mixer inverse -> rotor thrusts,
-// clamped to the reachable range -> desired rotor speeds.  Evaluated in FP64
-// (a few dozen operations per agent and sub-step; see DynConsts).
-__device__ __forceinline__ void controller(const DynConsts& c, const float Om_f[3], const float u[4],
-                                           float omega_des[4], CtrlTape* tape) {
-    const double Om[3] = {Om_f[0], Om_f[1], Om_f[2]};
-    const double L[3] = {c.dJ[0] * Om[0], c.dJ[1] * Om[1], c.dJ[2] * Om[2]};
-    const double gyro[3] = {Om[1] * L[2] - Om[2] * L[1], Om[2] * L[0] - Om[0] * L[2], Om[0] * L[1] - Om[1] * L[0]};
-    double rhs[4];
-    rhs[0] = ((double)u[0] + 1.0) * c.dhalf_a_max_m;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) rhs[j + 1] = c.dJK[j] * ((double)u[j + 1] * c.drate_max[j] - Om[j]) + gyro[j];
+// Thrust allocation shared by the controllers, in FP64: rotor thrusts
+// f = Ainv (collective thrust, moment), clamped to the reachable range, and
+// the desired rotor speeds from the thrust polynomial's positive root.
+__device__ __forceinline__ void allocate(const DynConsts& c, const double rhs[4], float omega_des[4],
+                                         CtrlTape* tape) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const double f = c.dAinv[i][0] * rhs[0] + c.dAinv[i][1] * rhs[1] + c.dAinv[i][2] * rhs[2] +
@@ -85,6 +77,144 @@ __device__ __forceinline__ void controller(const DynConsts& c, const float Om_f[
             tape->in_w[i] = in_w;
         }
     }
+}
+
+__device__ __forceinline__ void dcross(const double a[3], const double b[3], double r[3]) {
+    r[0] = a[1] * b[2] - a[2] * b[1];
+    r[1] = a[2] * b[0] - a[0] * b[2];
+    r[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// CTBR: u0 -> collective thrust m a, u1..3 -> desired rates; P rate loop with
+// gyroscopic feed-forward -> desired moment (Sec. III-A; the action type of the
+// paper's examples, Sec. IV).
+__device__ __forceinline__ void ctbr_rhs(const DynConsts& c, const float Om_f[3], const float u[4], double rhs[4]) {
+    const double Om[3] = {Om_f[0], Om_f[1], Om_f[2]};
+    const double L[3] = {c.dJ[0] * Om[0], c.dJ[1] * Om[1], c.dJ[2] * Om[2]};
+    double gyro[3];
+    dcross(Om, L, gyro);
+    rhs[0] = ((double)u[0] + 1.0) * c.dhalf_a_max_m;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) rhs[j + 1] = c.dJK[j] * ((double)u[j + 1] * c.drate_max[j] - Om[j]) + gyro[j];
+}
+
+// LV / PS (geometric control with yaw, after Lee et al. 2010): desired force
+// from the velocity (LV) or position and velocity (PS) errors plus gravity;
+// collective thrust = its projection on body z; desired attitude from the
+// force direction and the yaw command; moment from the attitude and rate
+// errors plus the gyroscopic term.  u = (target, yaw) in m or m/s and rad.
+__device__ void geometric_rhs(const DynConsts& c, const float y[17], const float u[4], bool position,
+                              double rhs[4]) {
+    const double q[4] = {y[6], y[7], y[8], y[9]};
+    const double inv_n = 1.0 / (q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    const double w = q[0], x = q[1], yy = q[2], z = q[3];
+    double R[3][3];
+    R[0][0] = (w * w + x * x - yy * yy - z * z) * inv_n;
+    R[0][1] = 2.0 * (x * yy - w * z) * inv_n;
+    R[0][2] = 2.0 * (x * z + w * yy) * inv_n;
+    R[1][0] = 2.0 * (x * yy + w * z) * inv_n;
+    R[1][1] = (w * w - x * x + yy * yy - z * z) * inv_n;
+    R[1][2] = 2.0 * (yy * z - w * x) * inv_n;
+    R[2][0] = 2.0 * (x * z - w * yy) * inv_n;
+    R[2][1] = 2.0 * (yy * z + w * x) * inv_n;
+    R[2][2] = (w * w - x * x - yy * yy + z * z) * inv_n;
+    double F[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const double acc = position ? (-c.dKpos[j] * ((double)y[j] - (double)u[j]) - c.dKvel[j] * (double)y[3 + j])
+                                    : (-c.dKvel[j] * ((double)y[3 + j] - (double)u[j]));
+        F[j] = c.dmass * acc;
+    }
+    F[2] += c.dmass * c.dg;
+    const double f_coll = F[0] * R[0][2] + F[1] * R[1][2] + F[2] * R[2][2];
+    const double nF = sqrt(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
+    double b3[3] = {0.0, 0.0, 1.0};
+    if (nF >= 1e-9) {
+        b3[0] = F[0] / nF;
+        b3[1] = F[1] / nF;
+        b3[2] = F[2] / nF;
+    }
+    double sy, cy;
+    sincos((double)u[3], &sy, &cy);
+    double c1[3] = {cy, sy, 0.0}, b2[3];
+    dcross(b3, c1, b2);
+    double n2 = sqrt(b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]);
+    if (n2 < 1e-6) {
+        const double c1b[3] = {-sy, cy, 0.0};
+        dcross(b3, c1b, b2);
+        n2 = sqrt(b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]);
+    }
+    b2[0] /= n2;
+    b2[1] /= n2;
+    b2[2] /= n2;
+    double b1[3];
+    dcross(b2, b3, b1);
+    double Rd[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        Rd[i][0] = b1[i];
+        Rd[i][1] = b2[i];
+        Rd[i][2] = b3[i];
+    }
+    double M[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double a = 0.0, b = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                a += Rd[k][i] * R[k][j];
+                b += R[k][i] * Rd[k][j];
+            }
+            M[i][j] = a - b;
+        }
+    const double eR[3] = {0.5 * M[2][1], 0.5 * M[0][2], 0.5 * M[1][0]};
+    const double Om[3] = {y[10], y[11], y[12]};
+    const double L[3] = {c.dJ[0] * Om[0], c.dJ[1] * Om[1], c.dJ[2] * Om[2]};
+    double gyro[3];
+    dcross(Om, L, gyro);
+    rhs[0] = f_coll;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) rhs[j + 1] = c.dJ[j] * (-c.dKatt[j] * eR[j] - c.dKom[j] * Om[j]) + gyro[j];
+}
+
+// Desired rotor speeds from the selected controller.
+__device__ __forceinline__ void controller(const DynConsts& c, const float y[17], const float u[4],
+                                           float omega_des[4], CtrlTape* tape) {
+    if (c.controller == 1) {
+        // SRT: u_i in [-1, 1] -> rotor i's thrust (u_i + 1) / 2 * f(omega_max)
+        const double fh = c.df_hi;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const double f = ((double)u[i] + 1.0) * 0.5 * fh;
+            const bool in_f = f >= c.df_lo && f <= c.df_hi;
+            const double fc = fmin(fmax(f, c.df_lo), c.df_hi);
+            double w, dw;
+            if (c.dk[2] != 0.0) {
+                const double disc = c.dk[1] * c.dk[1] - 4.0 * c.dk[2] * (c.dk[0] - fc);
+                const double sq = sqrt(fmax(disc, 0.0));
+                w = (sq - c.dk[1]) / (2.0 * c.dk[2]);
+                dw = disc > 0.0 ? 1.0 / sq : 0.0;
+            } else {
+                w = (fc - c.dk[0]) / c.dk[1];
+                dw = 1.0 / c.dk[1];
+            }
+            const bool in_w = w >= c.domega_min && w <= c.domega_max;
+            omega_des[i] = (float)fmin(fmax(w, c.domega_min), c.domega_max);
+            if (tape) {
+                tape->fc[i] = (float)fc;
+                tape->dw_df[i] = (float)dw;
+                tape->in_f[i] = in_f;
+                tape->in_w[i] = in_w;
+            }
+        }
+        return;
+    }
+    double rhs[4];
+    if (c.controller == 2 || c.controller == 3) geometric_rhs(c, y, u, c.controller == 3, rhs);
+    else ctbr_rhs(c, y + 10, u, rhs);
+    allocate(c, rhs, omega_des, tape);
 }
 
 // Eq. 1 right-hand side for y = (x, v, q, Omega) with body thrust (0,0,Fz) and
@@ -124,7 +254,7 @@ __device__ __forceinline__ void rhs(const DynConsts& c, const float y[13], float
 __device__ __forceinline__ void rotors(const DynConsts& c, float y[17], const float u[4], float& Fz, float eta[3],
                                        CtrlTape* tape) {
     float wd[4];
-    controller(c, y + 10, u, wd, tape);
+    controller(c, y, u, wd, tape);
     Fz = 0.0f;
     eta[0] = eta[1] = eta[2] = 0.0f;
 #pragma unroll
@@ -385,6 +515,14 @@ __device__ void substep_vjp(const DynConsts& c, const float y_in[17], const floa
         gin[13 + i] = wb * c.decay;
         const float wdb = tape.in_w[i] ? wb * (1.0f - c.decay) : 0.0f;
         fb[i] = tape.in_f[i] ? wdb * tape.dw_df[i] : 0.0f;
+    }
+    if (c.controller == 1) {
+        // SRT: f_i = (u_i + 1) / 2 * f(omega_max)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) gu[i] += fb[i] * 0.5f * c.f_hi;
+#pragma unroll
+        for (int j = 0; j < 13; ++j) gin[j] = yb[j];
+        return;
     }
     // controller: f = Ainv * rhs
     float rb[4];

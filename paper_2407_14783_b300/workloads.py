@@ -48,6 +48,11 @@ DEFAULT_PARAMS: dict = {
     "fov_deg": 90.0,                     # horizontal and vertical field of view
     "max_depth": 10.0,                   # m; beyond this a ray is a miss
     "cam_off": (0.0, 0.0, 0.0),          # camera origin in the body frame, m
+    "controller": 0,                     # 0 CTBR, 1 SRT, 2 LV (velocity + yaw), 3 PS (position + yaw)
+    "K_pos": (4.0, 4.0, 6.0),            # LV / PS gains: position 1/s^2, velocity 1/s,
+    "K_vel": (4.0, 4.0, 6.0),            # attitude 1/s^2, body rate 1/s
+    "K_att": (150.0, 150.0, 40.0),
+    "K_omega": (20.0, 20.0, 10.0),
 }
 
 # Rotor spin directions, rotor i at azimuth 45 + 90 i degrees.
