@@ -49,8 +49,10 @@ struct RenderArgs {
     long long* counters; // traversal counters (COUNT builds)
     // Longest-first scheduling state carried between launches (may be null):
     // sched[0..1] cost sums, sched[2..3] heavy-list lengths, sched[4] epoch,
-    // sched[5] item count of the launch that wrote the lists; heavy[2][cap]
-    // item lists; done[cap] marks of items already rendered in this launch.
+    // sched[5] item count of the launch that wrote the lists, sched[6..7]
+    // split-list lengths; heavy[2][cap] item lists (heavy items from the front,
+    // very heavy ones to split from the back, each at most cap / 2); done[cap]
+    // marks of items already rendered in this launch.
     unsigned long long* sched;
     unsigned* heavy;
     unsigned long long* done;

@@ -7,7 +7,8 @@
 //   2. triangles whose AABB spans more than a quarter of the scene's largest
 //      extent (room walls, floors) are kept out of the tree in a short list
 //      tested by every ray; the rest get 30-bit Morton codes (10 bits per axis)
-//      of their centroids, normalised to the centroid AABB;
+//      of their centroids on a cubic grid over the centroid AABB (the same cell
+//      size on every axis);
 //   3. a stable LSD radix sort of (code, triangle) pairs, 8 bits per pass;
 //   4. the binary radix tree over the sorted codes (Karras, HPG 2012): each
 //      internal node finds its key range and split from longest common
@@ -137,8 +138,11 @@ __global__ void morton_kernel(int n, const float4* __restrict__ tlo, const float
     uint32_t code = 0;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const float lo = unordered(cbounds[j]), hi = unordered(cbounds[3 + j]);
-        const float ext = hi - lo;
+        // one cell size for all three axes (the largest extent): in a flat room
+        // the top levels then split the long axes first
+        const float lo = unordered(cbounds[j]);
+        const float ext = fmaxf(fmaxf(unordered(cbounds[3]) - unordered(cbounds[0]), unordered(cbounds[4]) - unordered(cbounds[1])),
+                                unordered(cbounds[5]) - unordered(cbounds[2]));
         float t = ext > 0.0f ? (c[j] - lo) / ext : 0.0f;
         t = fminf(fmaxf(t, 0.0f), 1.0f);
         const uint32_t q = min((uint32_t)(t * 1024.0f), 1023u);

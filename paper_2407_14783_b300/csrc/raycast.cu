@@ -33,6 +33,7 @@ constexpr float kTmin = 1e-6f;
 constexpr int kIterCap = 1 << 18;  // node + leaf visits per work item
 constexpr int kStack = 64;
 constexpr int kWarpsPerCta = 4;
+constexpr int kSplit = 4;  // sub-packets (quarter tiles) of a very heavy tile
 
 struct Ray {
     float o[3], d[3], inv[3], ood[3];
@@ -160,30 +161,51 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_k
     unsigned n_heavy = 0;
     float thr = 0.0f;
     int rd = 0;
+    unsigned n_split = 0;
     if (sched) {
         const unsigned ep = (unsigned)A.sched[4];
         rd = ep & 1;
         mark = ((unsigned long long)A.launch_id << 32) | ep;
         if ((long long)A.sched[5] == total) {
-            n_heavy = (unsigned)min((unsigned long long)total, A.sched[2 + rd]);
+            const unsigned long long half = (unsigned long long)(A.sched_cap / 2);
+            n_split = (unsigned)min(min((unsigned long long)total, half), A.sched[6 + rd]);
+            n_heavy = (unsigned)min(min((unsigned long long)total - n_split, half), A.sched[2 + rd]);
             thr = 2.0f * (float)A.sched[rd] / (float)total;
         }
     }
+    // Splitting pays only when the launch is short enough for its longest tile
+    // to matter: at most 12 tiles per resident warp.
+    const bool allow_split = total <= 12ll * gridDim.x * kWarpsPerCta;
+    if (!allow_split) n_split = 0;
+    // Very heavy tiles (over twice the heavy threshold; a few per launch) run
+    // first, each as kSplit quarter-tile sub-packets on separate warps: a quarter
+    // walks only its own rays' paths, which shortens the longest dependent chain
+    // of node fetches.  Then the other heavy tiles, then the rest.
+    const long long n_first = (long long)n_split * kSplit;
     for (;;) {
         long long item = 0;
+        int sub = -1;
         if (lane == 0) {
             const long long k = (long long)atomicAdd(A.counter, 1u);
-            if (k < (long long)n_heavy) {
-                item = A.heavy[(size_t)rd * A.sched_cap + k];
-                // an entry from a concurrent launch of another size may not fit this one
+            if (k < n_first) {
+                // split list: stored from the end of the heavy array
+                item = A.heavy[(size_t)rd * A.sched_cap + (A.sched_cap - 1 - k / kSplit)];
+                sub = (int)(k % kSplit);
+            } else if (k < n_first + (long long)n_heavy) {
+                item = A.heavy[(size_t)rd * A.sched_cap + (k - n_first)];
+            } else {
+                item = k - n_first - n_heavy;
+                if (sched && item < total && __ldcg(A.done + item) == mark) item = -1;  // done in the first pass
+                if (item >= total) item = total;                                      // no work left
+            }
+            // an entry from a concurrent launch of another size may not fit this one
+            if (k < n_first + (long long)n_heavy) {
                 if (item < total) __stcg(A.done + item, mark);
                 else item = -1;
-            } else {
-                item = k - n_heavy;
-                if (sched && item < total && __ldcg(A.done + item) == mark) item = -1;  // done in the first pass
             }
         }
         item = __shfl_sync(kFull, item, 0);
+        sub = __shfl_sync(kFull, sub, 0);
         if (item < 0) continue;
         if (item >= total) break;
         // after a device-detected fault every warp stops taking work
@@ -227,6 +249,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_k
 
         Ray ray[RPL];
         int pix_r[RPL], pix_c[RPL];
+        bool mine_q[RPL];
         float flo[3] = {o[0], o[1], o[2]}, fhi[3] = {o[0], o[1], o[2]};  // ray-segment bounds
 #pragma unroll
         for (int q = 0; q < RPL; ++q) {
@@ -237,7 +260,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_k
             const float dB[3] = {1.0f, -(float)(2 * c + 1 - W) * 0.5f * A.cam.pix,
                                  -(float)(2 * r + 1 - H) * 0.5f * A.cam.pix};
             Ray& ry = ray[q];
-            ry.live = scene_ok && r < H && c < W;
+            const bool mine = sub < 0 || ((p % TW) / (TW / 2) == (sub & 1) && (p / TW) / (TH / 2) == (sub >> 1));
+            mine_q[q] = mine;
+            ry.live = scene_ok && r < H && c < W && mine;
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
                 ry.o[j] = o[j];
@@ -411,7 +436,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_k
         const size_t frame = (size_t)agent * H * W;
 #pragma unroll
         for (int q = 0; q < RPL; ++q) {
-            const bool in = pix_r[q] < H && pix_c[q] < W;
+            const bool in = pix_r[q] < H && pix_c[q] < W && mine_q[q];
             const size_t off = frame + (size_t)pix_r[q] * W + pix_c[q];
             const NoiseParams& nz = A.noise;
             const unsigned long long nb =
@@ -443,7 +468,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_k
         }
         if (A.rgb) {
             __syncwarp();
-            if ((W % 4) == 0 && (TW % 4) == 0 && tx0 + TW <= W && ty0 + TH <= H &&
+            if (sub < 0 && (W % 4) == 0 && (TW % 4) == 0 && tx0 + TW <= W && ty0 + TH <= H &&
                 (reinterpret_cast<uintptr_t>(A.rgb) & 3) == 0) {
                 // each tile row is TW*3 bytes starting at a 4-byte-aligned offset
                 constexpr int words_per_row = TW * 3 / 4;
@@ -457,7 +482,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_k
             } else {
 #pragma unroll
                 for (int q = 0; q < RPL; ++q) {
-                    if (pix_r[q] < H && pix_c[q] < W) {
+                    if (pix_r[q] < H && pix_c[q] < W && mine_q[q]) {
                         const int p = lane + 32 * q;
                         uint8_t* dst = A.rgb + 3 * (frame + (size_t)pix_r[q] * W + pix_c[q]);
                         dst[0] = rgbstage[3 * p];
@@ -472,9 +497,17 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_k
         if (sched && lane == 0) {
             const int wr = rd ^ 1;
             atomicAdd(&A.sched[wr], (unsigned long long)item_cost);
-            if (thr > 0.0f && (float)item_cost > thr) {
-                const unsigned long long k = atomicAdd(&A.sched[2 + wr], 1ull);
-                if (k < (unsigned long long)A.sched_cap) A.heavy[(size_t)wr * A.sched_cap + k] = (unsigned)item;
+            // a split tile is judged by its first quarter, scaled to the whole tile
+            const float est = sub < 0 ? (float)item_cost : (float)(item_cost * kSplit);
+            if (thr > 0.0f && sub <= 0 && est > thr) {
+                if (allow_split && est > 2.0f * thr) {
+                    const unsigned long long k = atomicAdd(&A.sched[6 + wr], 1ull);
+                    if (k < (unsigned long long)A.sched_cap / 2)
+                        A.heavy[(size_t)wr * A.sched_cap + (A.sched_cap - 1 - k)] = (unsigned)item;
+                } else {
+                    const unsigned long long k = atomicAdd(&A.sched[2 + wr], 1ull);
+                    if (k < (unsigned long long)A.sched_cap / 2) A.heavy[(size_t)wr * A.sched_cap + k] = (unsigned)item;
+                }
             }
         }
     }
@@ -508,6 +541,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_k
                 // this launch's read slot becomes the next launch's write slot
                 A.sched[rd] = 0ull;
                 A.sched[2 + rd] = 0ull;
+                A.sched[6 + rd] = 0ull;
                 A.sched[5] = (unsigned long long)total;
                 A.sched[4] = A.sched[4] + 1ull;
             }
