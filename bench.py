@@ -254,7 +254,7 @@ def run_ours(args):
         best = sim.render_config()
     else:
         best, times = sim.autotune(ids, state, depth, rgb, iters=3)
-        tune = {"{tile_w}x{tile_h}/rpl{rays_per_lane}/{s}stack/{g}".format(
+        tune = {"{tile_w}x{tile_h}/rpl{rays_per_lane}/{s}stack/{g}/bvh{node_width}".format(
                     s="smem" if c["stack_in_smem"] else "reg", g="staged" if c["stage_in_smem"] else "bcast", **c):
                 round(t, 4) for c, t in zip(Sim.render_configs(), times)}
     for t in range(W):

@@ -336,6 +336,7 @@ int sim_server_destroy(sim_server* srv);
  *   same address, a broadcast through L1). */
 typedef struct sim_render_config {
     int32_t tile_w, tile_h, rays_per_lane, stack_in_smem, stack_depth, warps_per_cta, ctas_per_sm, stage_in_smem;
+    int32_t node_width;  /* 2: binary BVH nodes; 4: 4-wide nodes (two binary levels per fetch) */
 } sim_render_config;
 int sim_get_render_config(const sim_ctx* ctx, sim_render_config* cfg);
 int sim_set_render_config(sim_ctx* ctx, const sim_render_config* cfg);

@@ -49,7 +49,7 @@ class RenderConfig(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("rays_per_lane", ctypes.c_int32),
                 ("stack_in_smem", ctypes.c_int32), ("stack_depth", ctypes.c_int32),
                 ("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("stage_in_smem", ctypes.c_int32)]
+                ("stage_in_smem", ctypes.c_int32), ("node_width", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

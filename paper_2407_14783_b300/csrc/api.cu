@@ -36,7 +36,7 @@ constexpr int kRing = 64;  // work-counter slots, so renders on different stream
 struct SceneRec {
     bool live = false;
     int32_t* labels = nullptr;  // segmentation labels per triangle (owned), or null
-    void* mem[4] = {nullptr, nullptr, nullptr, nullptr};
+    void* mem[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     size_t bytes = 0;
     int64_t n_tris = 0;
     LbvhResult r{};
@@ -77,7 +77,7 @@ struct sim_ctx {
     size_t sched_bytes = 0;
     int sched_cap = 0;
     long long* d_stats = nullptr;
-    sim_render_config rcfg{8, 4, 1, 0, 64, 4, 0, 0};  // fastest measured on the large scene
+    sim_render_config rcfg{8, 4, 1, 0, 64, 4, 0, 0, 2};  // fastest measured on the large scene
     // staging for sim_env_step
     float* d_cmd = nullptr;
     float* d_depth = nullptr;
@@ -248,6 +248,7 @@ int upload_table(sim_ctx* c) {
             continue;
         }
         r.nodes = s.r.nodes;
+        r.wide = s.r.wide;
         r.tris = s.r.tris;
         r.large = s.r.large;
         r.colors = s.r.colors;
@@ -255,6 +256,8 @@ int upload_table(sim_ctx* c) {
         r.root = s.r.root;
         r.n_large = s.r.n_large;
         r.depth = s.r.depth;
+        r.n_nodes = s.r.n_nodes;
+        r.n_tree_tris = s.r.n_bvh;
     }
     if (n) {
         cudaError_t e = cudaMemcpy(c->d_table, rows.data(), sizeof(SceneRow) * n, cudaMemcpyHostToDevice);
@@ -278,11 +281,20 @@ struct AllocCtx {
     int status;
 };
 
+// Device buffers of a scene: binary nodes, 4-wide nodes, triangles, large triangles, colours.
+void scene_sizes(const LbvhResult& r, int64_t n_tris, size_t sz[5]) {
+    sz[0] = (size_t)r.n_nodes * 64;
+    sz[1] = (size_t)r.n_bvh * 48;
+    sz[2] = (size_t)r.n_large * 48;
+    sz[3] = (size_t)n_tris * 4;
+    sz[4] = (size_t)r.n_nodes * 128;
+}
+
 cudaError_t scene_alloc(void* user, LbvhResult* r) {
     AllocCtx* a = (AllocCtx*)user;
-    const size_t sz[4] = {(size_t)r->n_nodes * 64, (size_t)r->n_bvh * 48, (size_t)r->n_large * 48,
-                          (size_t)a->n_tris * 4};
-    for (int i = 0; i < 4; ++i) {
+    size_t sz[5];
+    scene_sizes(*r, a->n_tris, sz);
+    for (int i = 0; i < 5; ++i) {
         int rc = ctx_alloc(a->c, sz[i], &a->rec->mem[i]);
         if (rc) {
             a->status = rc;
@@ -294,15 +306,16 @@ cudaError_t scene_alloc(void* user, LbvhResult* r) {
     r->tris = (float4*)a->rec->mem[1];
     r->large = (float4*)a->rec->mem[2];
     r->colors = (uint32_t*)a->rec->mem[3];
+    r->wide = (float4*)a->rec->mem[4];
     return cudaSuccess;
 }
 
 void free_scene(sim_ctx* c, SceneRec& s) {
     if (s.labels) ctx_free(c, s.labels, sizeof(int32_t) * (size_t)std::max<int64_t>(s.n_tris, 1));
     s.labels = nullptr;
-    const size_t sz[4] = {(size_t)s.r.n_nodes * 64, (size_t)s.r.n_bvh * 48, (size_t)s.r.n_large * 48,
-                          (size_t)s.n_tris * 4};
-    for (int i = 0; i < 4; ++i) {
+    size_t sz[5];
+    scene_sizes(s.r, s.n_tris, sz);
+    for (int i = 0; i < 5; ++i) {
         if (s.mem[i]) ctx_free(c, s.mem[i], sz[i]);
         s.mem[i] = nullptr;
     }
@@ -334,6 +347,11 @@ RenderArgs render_args(sim_ctx* c, int n, const int32_t* soa, const float* state
     a.seg = nullptr;
     a.noise = c->noise;
     a.noise_frame = c->d_noise_frame;
+    // stream the resident scenes into L2 at launch start when they fit in it
+    size_t scene_bytes = 0;
+    for (const auto& sc : c->scenes)
+        if (sc.live) scene_bytes += (size_t)sc.r.n_nodes * 64 + (size_t)sc.r.n_bvh * 48 + (size_t)sc.r.n_large * 48;
+    a.prefetch_l2 = scene_bytes <= ((size_t)64 << 20) ? 1 : 0;
     a.err = c->d_err;
     a.counters = c->d_stats;
     return a;
@@ -571,9 +589,9 @@ int sim_create_scene(sim_ctx* c, const float* verts, int64_t n_verts, const int3
     }
     cleanup();
     if (e != cudaSuccess) {
-        for (int i = 0; i < 4; ++i) {
-            const size_t sz[4] = {(size_t)rec.r.n_nodes * 64, (size_t)rec.r.n_bvh * 48, (size_t)rec.r.n_large * 48,
-                                  (size_t)n_tris * 4};
+        size_t sz[5];
+        scene_sizes(rec.r, n_tris, sz);
+        for (int i = 0; i < 5; ++i) {
             if (rec.mem[i]) ctx_free(c, rec.mem[i], sz[i]);
         }
         if (ac.status) return ac.status;
@@ -930,21 +948,39 @@ int sim_autotune_render(sim_ctx* c, int32_t n, const int32_t* soa, const float* 
     if (iters < 1 || !best) return fail(SIM_ERR_INVALID_ARG, "bad autotune arguments");
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
-    sim_render_config cfgs[64];
-    const int nc = render_config_list(cfgs, 64);
+    sim_render_config cfgs[128];
+    const int nc = render_config_list(cfgs, 128);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best_ms = 1e30f;
     int best_i = -1;
     const int need_depth = max_scene_depth(c);
+    // every configuration is timed as sim_render runs it: with scheduling hints,
+    // from its own fresh hint buffer (two warm-up launches build the hints)
+    long long max_items = 0;
+    for (int i = 0; i < nc; ++i) max_items = std::max(max_items, render_items(c, n, cfgs[i]));
+    const int scap = (int)std::max<long long>(1, max_items);
+    void* smem = nullptr;
+    if ((rc = sched_alloc(c, scap, &smem, s))) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return rc;
+    }
     for (int i = 0; i < nc; ++i) {
         sim_render_config cf = cfgs[i];
         if (need_depth >= cf.stack_depth) continue;
-        rc = do_render(c, n, soa, state, depth, rgb, nullptr, false, cf, s);  // warm-up
+        cudaError_t me = cudaMemsetAsync(smem, 0, sched_bytes_for(scap), s);
+        if (me != cudaSuccess) {
+            rc = cuda_fail(me, "autotune reset");
+            break;
+        }
+        for (int w = 0; w < 2 && !rc; ++w)
+            rc = do_render(c, n, soa, state, depth, rgb, nullptr, false, cf, s, nullptr, smem, scap);  // warm-up
         if (rc) break;
         cudaEventRecord(e0, s);
-        for (int k = 0; k < iters && !rc; ++k) rc = do_render(c, n, soa, state, depth, rgb, nullptr, false, cf, s);
+        for (int k = 0; k < iters && !rc; ++k)
+            rc = do_render(c, n, soa, state, depth, rgb, nullptr, false, cf, s, nullptr, smem, scap);
         cudaEventRecord(e1, s);
         cudaError_t e = cudaEventSynchronize(e1);
         if (rc) break;
@@ -963,6 +999,8 @@ int sim_autotune_render(sim_ctx* c, int32_t n, const int32_t* soa, const float* 
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    ctx_free(c, smem, sched_bytes_for(scap));
     if (rc) return rc;
     if (best_i < 0) return fail(SIM_ERR_INVALID_ARG, "no configuration fits the scene depth");
     c->rcfg = cfgs[best_i];

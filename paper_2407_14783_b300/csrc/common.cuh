@@ -56,6 +56,7 @@ struct CamConsts {
 // range (see leaf_code); kEmptyRoot when the BVH holds no triangle.
 struct SceneRow {
     const float4* nodes;     // 4 float4 per internal node
+    const float4* wide;      // 8 float4 per internal node: 4-wide layout of the even-depth ones
     const float4* tris;      // 3 float4 per triangle, leaf order
     const float4* large;     // 3 float4 per large triangle (tested by every ray)
     const uint32_t* colors;  // RGB8 per original triangle id
@@ -64,6 +65,8 @@ struct SceneRow {
     int32_t n_large;
     int32_t depth;
     int32_t live;
+    int32_t n_nodes;         // internal nodes (binary layout)
+    int32_t n_tree_tris;     // triangles in the tree (leaf order)
 };
 
 __host__ __device__ inline int32_t leaf_code(int32_t first, int32_t count) {

@@ -21,12 +21,14 @@ struct LbvhResult {
     float lo[3], hi[3];
     int n_large, n_bvh, n_nodes, depth, root;
     float4* nodes;
+    float4* wide;  // 8 float4 per internal node (valid at even depth): the 4-wide layout
     float4* tris;
     float4* large;
     uint32_t* colors;
 };
-// Called once the counts are known; must allocate nodes (4 float4 each), tris
-// (3 float4 each, n_bvh), large (3 float4 each, n_large), colors (n_tris).
+// Called once the counts are known; must allocate nodes (4 float4 each), wide
+// (8 float4 each), tris (3 float4 each, n_bvh), large (3 float4 each, n_large),
+// colors (n_tris).
 typedef cudaError_t (*LbvhAlloc)(void* user, LbvhResult* r);
 size_t lbvh_scratch_bytes(int64_t nt);
 cudaError_t lbvh_build(int64_t nt, const float* d_verts, const int* d_tris, const uint8_t* d_rgb, void* scratch,
@@ -61,6 +63,7 @@ struct RenderArgs {
     int32_t* seg;        // segmentation image [n][H][W] or null
     NoiseParams noise;
     unsigned long long* noise_frame;  // frame counter of the noise streams (advanced by every noisy launch)
+    int prefetch_l2;     // stream every live scene's nodes and triangles into L2 at launch start
 };
 size_t render_smem_bytes(int warps_per_cta, int stack_depth, int rpl);
 int render_config_list(sim_render_config* out, int max);

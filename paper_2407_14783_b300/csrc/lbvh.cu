@@ -362,6 +362,68 @@ __global__ void pack_nodes_kernel(int n, const uint32_t* __restrict__ order, con
                                            __int_as_float(child_code(c.y, range)), 0.0f, 0.0f);
 }
 
+// Depth parity of every internal node (root: even).
+__global__ void depth_parity_kernel(int n, const int* __restrict__ parent_int, int* __restrict__ parity) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = 0;
+    for (int p = parent_int[i]; p >= 0 && d <= kMaxTreeDepth; p = parent_int[p]) ++d;
+    parity[i] = d & 1;
+}
+
+// 4-wide node of every even-depth internal node i: its children, with every
+// child that is an internal node (more than kLeafMax triangles) replaced by that
+// child's two children -- which sit at even depth again.  Layout (8 float4):
+// lo.x, lo.y, lo.z, hi.x, hi.y, hi.z of the four slots, then the four child
+// codes; unused slots hold kEmptyRoot and a point box far outside the scene.
+__global__ void pack_wide_kernel(int n, const uint32_t* __restrict__ order, const float4* __restrict__ tlo,
+                                 const float4* __restrict__ thi, const int2* __restrict__ child,
+                                 const int2* __restrict__ range, const float4* __restrict__ node_lo,
+                                 const float4* __restrict__ node_hi, const int* __restrict__ parity, float pad,
+                                 float4* __restrict__ wide) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1 || parity[i]) return;
+    float bl[4][3], bh[4][3];
+    int code[4];
+    int k = 0;
+    const int2 c = child[i];
+    for (int s = 0; s < 2; ++s) {
+        const int cc = s == 0 ? c.x : c.y;
+        const int cd = child_code(cc, range);
+        if (cd >= 0) {
+            const int2 g = child[cd];
+            for (int t = 0; t < 2; ++t) {
+                const int gg = t == 0 ? g.x : g.y;
+                float4 lo, hi;
+                child_box(gg, order, tlo, thi, node_lo, node_hi, pad, lo, hi);
+                bl[k][0] = lo.x; bl[k][1] = lo.y; bl[k][2] = lo.z;
+                bh[k][0] = hi.x; bh[k][1] = hi.y; bh[k][2] = hi.z;
+                code[k++] = child_code(gg, range);
+            }
+        } else {
+            float4 lo, hi;
+            child_box(cc, order, tlo, thi, node_lo, node_hi, pad, lo, hi);
+            bl[k][0] = lo.x; bl[k][1] = lo.y; bl[k][2] = lo.z;
+            bh[k][0] = hi.x; bh[k][1] = hi.y; bh[k][2] = hi.z;
+            code[k++] = cd;
+        }
+    }
+    for (; k < 4; ++k) {
+        for (int j = 0; j < 3; ++j) bl[k][j] = bh[k][j] = 1.0e30f;
+        code[k] = kEmptyRoot;
+    }
+    float4* w = wide + 8 * (size_t)i;
+    w[0] = make_float4(bl[0][0], bl[1][0], bl[2][0], bl[3][0]);
+    w[1] = make_float4(bl[0][1], bl[1][1], bl[2][1], bl[3][1]);
+    w[2] = make_float4(bl[0][2], bl[1][2], bl[2][2], bl[3][2]);
+    w[3] = make_float4(bh[0][0], bh[1][0], bh[2][0], bh[3][0]);
+    w[4] = make_float4(bh[0][1], bh[1][1], bh[2][1], bh[3][1]);
+    w[5] = make_float4(bh[0][2], bh[1][2], bh[2][2], bh[3][2]);
+    w[6] = make_float4(__int_as_float(code[0]), __int_as_float(code[1]), __int_as_float(code[2]),
+                       __int_as_float(code[3]));
+    w[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 // Triangles in sorted order (first n_bvh go to the tree, the rest are large).
 __global__ void pack_tris_kernel(int n, int n_bvh, const uint32_t* __restrict__ order,
                                  const float* __restrict__ verts, const int* __restrict__ tris,
@@ -478,6 +540,9 @@ cudaError_t lbvh_build(int64_t nt, const float* d_verts, const int* d_tris, cons
         const float pad = 2.0e-5f * fmaxf(ext, 1e-3f);
         pack_nodes_kernel<<<nb(n_bvh - 1, 256), 256, 0, s>>>(n_bvh, va, tlo, thi, child, range, node_lo, node_hi,
                                                              pad, out->nodes);
+        depth_parity_kernel<<<nb(n_bvh - 1, 256), 256, 0, s>>>(n_bvh, parent_int, flags);
+        pack_wide_kernel<<<nb(n_bvh - 1, 256), 256, 0, s>>>(n_bvh, va, tlo, thi, child, range, node_lo, node_hi,
+                                                            flags, pad, out->wide);
         VF_TRY(cudaGetLastError());
         int2 rr;
         VF_TRY(cudaMemcpyAsync(&rr, range, sizeof(int2), cudaMemcpyDeviceToHost, s));

@@ -136,8 +136,10 @@ __device__ float noisy(float x, float hi, float gs, float sp, float shot, float 
     return fminf(fmaxf(x, 0.0f), hi);
 }
 
-template <int TW, int TH, int RPL, bool SMEM_STACK, bool STAGE, bool COUNT>
-__global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_kernel(RenderArgs A) {
+__device__ __forceinline__ float comp4(const float4& v, int s) { return s == 0 ? v.x : s == 1 ? v.y : s == 2 ? v.z : v.w; }
+
+template <int TW, int TH, int RPL, bool SMEM_STACK, bool STAGE, bool COUNT, bool WIDE>
+__global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6) raycast_kernel(RenderArgs A) {
     static_assert(TW * TH == 32 * RPL, "tile must hold 32 * RPL pixels");
     extern __shared__ float4 smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -154,6 +156,24 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_k
     long long c_nodes = 0, c_tris = 0, c_large = 0, c_items = 0, c_need_nodes = 0, c_need_tris = 0;
 
     const unsigned long long noise_frame = A.noise.enabled ? *A.noise_frame : 0ull;
+    if (A.prefetch_l2) {
+        // After an L2 flush the first walks would pay DRAM latency on every node of
+        // their dependent chains; the whole grid streams the scenes into L2 at
+        // once instead (one 128-byte line per prefetch, many in flight).
+        const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        const long long nthreads = (long long)gridDim.x * blockDim.x;
+        for (int sc = 0; sc < A.n_scenes; ++sc) {
+            const SceneRow& r = A.table[sc];
+            if (!r.live) continue;
+            const char* bases[3] = {(const char*)r.nodes, (const char*)r.tris, (const char*)r.large};
+            const long long lens[3] = {(long long)r.n_nodes * 64, (long long)r.n_tree_tris * 48,
+                                       (long long)r.n_large * 48};
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                for (long long off = tid * 128; off < lens[k]; off += nthreads * 128)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(bases[k] + off));
+        }
+    }
     // Longest-first order: tiles that cost more than twice the mean in the
     // previous launch (same item count) are handed out first, then all others.
     const bool sched = A.sched != nullptr && total <= A.sched_cap;
@@ -334,7 +354,90 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_k
                     break;
                 }
                 int next = kEmptyRoot;
-                if (cur >= 0) {
+                if (WIDE && cur >= 0) {
+                    // 4-wide node: SoA child boxes, codes in w[6]
+                    const float4* wp = row.wide + 8 * (size_t)cur;
+                    float4 w[7];
+                    if (STAGE) {
+                        __syncwarp();
+                        if (lane < 7) stage[lane] = __ldg(wp + lane);
+                        __syncwarp();
+#pragma unroll
+                        for (int k = 0; k < 7; ++k) w[k] = stage[k];
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 7; ++k) w[k] = __ldg(wp + k);
+                    }
+                    float key[4];
+                    int code[4], slot[4];
+                    bool hq[RPL][4];
+#pragma unroll
+                    for (int c4 = 0; c4 < 4; ++c4) {
+                        code[c4] = __float_as_int(comp4(w[6], c4));
+                        slot[c4] = c4;
+                        bool any = false;
+#pragma unroll
+                        for (int q = 0; q < RPL; ++q) {
+                            float tn;
+                            hq[q][c4] = code[c4] != kEmptyRoot &&
+                                        slab(ray[q], comp4(w[0], c4), comp4(w[1], c4), comp4(w[2], c4),
+                                             comp4(w[3], c4), comp4(w[4], c4), comp4(w[5], c4), tn);
+                            any |= hq[q][c4];
+                        }
+                        const unsigned b = __ballot_sync(kFull, any);
+                        // order key: distance from the common camera origin to the box centre
+                        const float cx = 0.5f * (comp4(w[0], c4) + comp4(w[3], c4)) - o[0];
+                        const float cy = 0.5f * (comp4(w[1], c4) + comp4(w[4], c4)) - o[1];
+                        const float cz = 0.5f * (comp4(w[2], c4) + comp4(w[5], c4)) - o[2];
+                        key[c4] = b ? cx * cx + cy * cy + cz * cz : 3.0e38f;
+                    }
+                    // sort the four (key, code, slot) triples ascending: 5 compare-exchanges
+#define VF_CX(a, b)                                                                            \
+    if (key[b] < key[a]) {                                                                     \
+        const float tk = key[a]; key[a] = key[b]; key[b] = tk;                                 \
+        const int tc = code[a]; code[a] = code[b]; code[b] = tc;                               \
+        const int ts = slot[a]; slot[a] = slot[b]; slot[b] = ts;                               \
+    }
+                    VF_CX(0, 1) VF_CX(2, 3) VF_CX(0, 2) VF_CX(1, 3) VF_CX(1, 2)
+#undef VF_CX
+                    const int cnt = (key[0] < 3.0e38f) + (key[1] < 3.0e38f) + (key[2] < 3.0e38f) + (key[3] < 3.0e38f);
+                    if (COUNT) {
+                        ++c_nodes;
+#pragma unroll
+                        for (int q = 0; q < RPL; ++q) c_need_nodes += need[q] ? 1 : 0;
+                    }
+                    if (cnt > 0) {
+                        if (sp + cnt - 1 > kStack) {
+                            if (lane == 0) set_error(A.err, kDevErrTraversal);
+                            break;
+                        }
+                        // push the farther hit children, farthest first
+                        for (int j = cnt - 1; j >= 1; --j) {
+                            const int far = j == 3 ? code[3] : j == 2 ? code[2] : code[1];
+                            if (SMEM_STACK) {
+                                if (lane == 0) sstack[sp] = far;
+                            } else if (lane == (sp & 31)) {
+                                if (sp < 32) reg0 = far; else reg1 = far;
+                            }
+                            if (COUNT) {
+                                const int sl = j == 3 ? slot[3] : j == 2 ? slot[2] : slot[1];
+#pragma unroll
+                                for (int q = 0; q < RPL; ++q) {
+                                    const bool nf = need[q] && (sl == 0 ? hq[q][0] : sl == 1 ? hq[q][1] : sl == 2 ? hq[q][2] : hq[q][3]);
+                                    needmask[q] = (needmask[q] & ~(1ull << sp)) | ((unsigned long long)nf << sp);
+                                }
+                            }
+                            ++sp;
+                        }
+                        next = code[0];
+                        if (COUNT) {
+                            const int sl = slot[0];
+#pragma unroll
+                            for (int q = 0; q < RPL; ++q)
+                                need[q] = need[q] && (sl == 0 ? hq[q][0] : sl == 1 ? hq[q][1] : sl == 2 ? hq[q][2] : hq[q][3]);
+                        }
+                    }
+                } else if (cur >= 0) {
                     const float4* np = row.nodes + 4 * (size_t)cur;
                     float4 n0, n1, n2, n3;
                     if (STAGE) {
@@ -550,21 +653,27 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, RPL == 1 ? 8 : 6) raycast_k
     }
 }
 
-template <int TW, int TH, int RPL, bool SMEM_STACK, bool STAGE, bool COUNT>
+template <int TW, int TH, int RPL, bool SMEM_STACK, bool STAGE, bool COUNT, bool WIDE>
 cudaError_t launch_one(const RenderArgs& a, int ctas, cudaStream_t s) {
-    auto k = raycast_kernel<TW, TH, RPL, SMEM_STACK, STAGE, COUNT>;
+    auto k = raycast_kernel<TW, TH, RPL, SMEM_STACK, STAGE, COUNT, WIDE>;
     const size_t shm = render_smem_bytes(kWarpsPerCta, kStack, RPL);
     return launch_cfg(reinterpret_cast<const void*>(k), a, kWarpsPerCta, ctas, shm, s);
 }
 
+template <int TW, int TH, int RPL, bool COUNT, bool WIDE>
+cudaError_t launch_shape_w(const RenderArgs& a, const sim_render_config& c, int ctas, cudaStream_t s) {
+    if (c.stack_in_smem) {
+        if (c.stage_in_smem) return launch_one<TW, TH, RPL, true, true, COUNT, WIDE>(a, ctas, s);
+        return launch_one<TW, TH, RPL, true, false, COUNT, WIDE>(a, ctas, s);
+    }
+    if (c.stage_in_smem) return launch_one<TW, TH, RPL, false, true, COUNT, WIDE>(a, ctas, s);
+    return launch_one<TW, TH, RPL, false, false, COUNT, WIDE>(a, ctas, s);
+}
+
 template <int TW, int TH, int RPL, bool COUNT>
 cudaError_t launch_shape(const RenderArgs& a, const sim_render_config& c, int ctas, cudaStream_t s) {
-    if (c.stack_in_smem) {
-        if (c.stage_in_smem) return launch_one<TW, TH, RPL, true, true, COUNT>(a, ctas, s);
-        return launch_one<TW, TH, RPL, true, false, COUNT>(a, ctas, s);
-    }
-    if (c.stage_in_smem) return launch_one<TW, TH, RPL, false, true, COUNT>(a, ctas, s);
-    return launch_one<TW, TH, RPL, false, false, COUNT>(a, ctas, s);
+    if (c.node_width == 4) return launch_shape_w<TW, TH, RPL, COUNT, true>(a, c, ctas, s);
+    return launch_shape_w<TW, TH, RPL, COUNT, false>(a, c, ctas, s);
 }
 
 template <bool COUNT>
@@ -586,23 +695,26 @@ size_t render_smem_bytes(int warps_per_cta, int stack_depth, int rpl) {
 int render_config_list(sim_render_config* out, int max) {
     static const int shapes[][3] = {{8, 4, 1}, {4, 8, 1}, {16, 2, 1}, {8, 8, 2}, {16, 4, 2}};
     int k = 0;
-    for (const auto& sh : shapes)
-        for (int stack = 0; stack <= 1; ++stack)
-            for (int stg = 0; stg <= 1; ++stg) {
-                if (k < max && out) out[k] = sim_render_config{sh[0], sh[1], sh[2], stack, kStack, kWarpsPerCta, 0, stg};
-                ++k;
-            }
+    for (int width : {2, 4})
+        for (const auto& sh : shapes)
+            for (int stack = 0; stack <= 1; ++stack)
+                for (int stg = 0; stg <= 1; ++stg) {
+                    if (k < max && out)
+                        out[k] = sim_render_config{sh[0], sh[1], sh[2], stack, kStack, kWarpsPerCta, 0, stg, width};
+                    ++k;
+                }
     return k;
 }
 
 bool render_config_valid(const sim_render_config& c) {
-    sim_render_config all[64];
-    const int n = render_config_list(all, 64);
+    sim_render_config all[128];
+    const int n = render_config_list(all, 128);
     for (int i = 0; i < n; ++i) {
         const sim_render_config& a = all[i];
         if (a.tile_w == c.tile_w && a.tile_h == c.tile_h && a.rays_per_lane == c.rays_per_lane &&
             (c.stack_in_smem == 0 || c.stack_in_smem == 1) && (c.stage_in_smem == 0 || c.stage_in_smem == 1) &&
-            c.warps_per_cta == kWarpsPerCta && c.stack_depth == kStack && c.ctas_per_sm >= 0 && c.ctas_per_sm <= 32)
+            c.warps_per_cta == kWarpsPerCta && c.stack_depth == kStack && c.ctas_per_sm >= 0 && c.ctas_per_sm <= 32 &&
+            (c.node_width == 2 || c.node_width == 4))
             return true;
     }
     return false;
