@@ -187,7 +187,8 @@ def _recorded_traffic():
         sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
         for line in open(prof):
             if line.startswith("dram_bytes_per_launch"):
-                parts = dict(kv.strip().split("=") for kv in line.split(";"))
+                parts = dict((k.strip(), v.strip()) for k, v in
+                             (kv.split("=", 1) for kv in line.split(";") if "=" in kv))
                 if parts.get("raycast_cu_sha1", "").strip() == sha:
                     return int(parts["dram_bytes_per_launch"].strip())
     except Exception:

@@ -200,13 +200,16 @@ int sim_scene_set_labels(sim_ctx* ctx, int32_t scene_id, const int32_t* labels, 
  * with L = k x, k = *_shot, skipped when 0), additive Gaussian (sigma *_gauss),
  * speckle (x' = x (1 + sigma z), sigma *_speckle), salt and pepper (probability
  * *_salt_pepper, then 0 or the maximum with equal chance), clamp to [0, max]
- * (max = max_depth for depth, 255 for colour, rounded to nearest even).  The
- * segmentation image loses a pixel's label (-1) with probability seg_dropout.
- * Hit ids are never noisy.  Draws come from SplitMix64 (Steele, Lea, Flood
- * 2014) as output number i of the stream `seed`, with
- * i = ((frame * n_agents + agent) * H * W + pixel) * 32 + slot (mod 2^64); slots:
- * depth 0-7, colour channel c 8+8c..15+8c, segmentation 30; within a block of 8:
- * Gaussian 0-1, speckle 2-3, shot 4-5, salt and pepper 6-7 (decision, value).
+ * (max = max_depth for depth, 255 for colour and seg_max for segmentation labels;
+ * colour and labels are then rounded half to even).  Label noise touches only
+ * labelled pixels (a miss stays -1) and needs seg_max > 0 and labels below 2^24;
+ * afterwards the segmentation image loses a pixel's label (-1) with probability
+ * seg_dropout.  Hit ids are never noisy.  Draws come from SplitMix64 (Steele,
+ * Lea, Flood 2014) as output number i of the stream `seed`, with
+ * i = ((frame * n_agents + agent) * H * W + pixel) * 64 + slot (mod 2^64); slots:
+ * depth 0-7, colour channel c 8+8c..15+8c, segmentation 32-39, segmentation
+ * dropout 40; within a block of 8: Gaussian 0-1, speckle 2-3, shot 4-5, salt
+ * and pepper 6-7 (decision, value).
  * A standard normal from slots (s, s+1): sqrt(-2 ln u1) cos(2 pi u2) with
  * u1 = (x1 >> 40 + 0.5) / 2^24 and u2 = (x2 >> 40) / 2^24; a uniform for a decision
  * is (x >> 40) / 2^24.  `frame` starts at first_frame and advances by one with
@@ -217,6 +220,8 @@ typedef struct sim_noise {
     float depth_gauss, depth_speckle, depth_shot, depth_salt_pepper;
     float rgb_gauss, rgb_speckle, rgb_shot, rgb_salt_pepper;
     float seg_dropout;
+    float seg_gauss, seg_speckle, seg_shot, seg_salt_pepper;
+    float seg_max;
 } sim_noise;
 int sim_set_noise(sim_ctx* ctx, const sim_noise* cfg);
 
@@ -246,13 +251,18 @@ int sim_rollout(sim_ctx* ctx, int32_t n_agents, int32_t T, int32_t K, const floa
 int sim_rollout_backward(sim_ctx* ctx, int32_t n_agents, int32_t T, int32_t K, const float* ckpt,
                          const float* cmds, const float* g_states, float* g_state0, float* g_cmds, void* stream);
 
-/* The environment step as a user calls it, with host buffers: copy the
- * commands in, step, render, copy the images (and optionally the state) out.
+/* The environment step as a user calls it, with host buffers: commands in,
+ * step, render, images (and optionally the state) out.
  *   cmd_host float32 [4][n]; depth_host float32 [n][H][W] or NULL; rgb_host
  *   uint8 [n][H][W][3] or NULL; state_host float32 [17][n] or NULL (post-step
  *   state).  The device state (state dev [17][n]) stays resident and is
- *   updated in place.  Asynchronous on `stream`; host buffers must stay valid
- *   until the stream reaches this point (pinned host memory for overlap). */
+ *   updated in place.  Page-locked host buffers (cudaHostAlloc, cudaMallocHost,
+ *   cudaHostRegister) are accessed in place by the kernels: the step kernel
+ *   reads the commands from host memory and the render writes the images into
+ *   host memory as tiles finish, so the download overlaps the ray cast.
+ *   Pageable buffers go through device staging and copies after the render.
+ *   Asynchronous on `stream`; host buffers must stay valid and untouched until
+ *   the stream reaches this point. */
 int sim_env_step(sim_ctx* ctx, int32_t n_agents, const int32_t* scene_of_agent, float* state,
                  const float* cmd_host, float* depth_host, uint8_t* rgb_host, float* state_host, void* stream);
 

@@ -66,7 +66,8 @@ class SimNoise(ctypes.Structure):
                 ("depth_speckle", ctypes.c_float), ("depth_shot", ctypes.c_float),
                 ("depth_salt_pepper", ctypes.c_float), ("rgb_gauss", ctypes.c_float),
                 ("rgb_speckle", ctypes.c_float), ("rgb_shot", ctypes.c_float), ("rgb_salt_pepper", ctypes.c_float),
-                ("seg_dropout", ctypes.c_float)]
+                ("seg_dropout", ctypes.c_float), ("seg_gauss", ctypes.c_float), ("seg_speckle", ctypes.c_float),
+                ("seg_shot", ctypes.c_float), ("seg_salt_pepper", ctypes.c_float), ("seg_max", ctypes.c_float)]
 
 
 class SimRequest(ctypes.Structure):

@@ -87,7 +87,10 @@ struct NoiseParams {
     unsigned long long seed;
     float d_gauss, d_speckle, d_shot, d_sp;   // depth: additive N(0,s^2) m, multiplicative, shot scale, salt&pepper
     float c_gauss, c_speckle, c_shot, c_sp;   // colour channels (0-255 units)
-    float s_sp;                               // segmentation: probability of an unlabelled pixel
+    float s_drop;                             // segmentation: probability of an unlabelled pixel
+    float s_gauss, s_speckle, s_shot, s_sp;   // segmentation label noise (label units)
+    float s_max;                              // largest label after noise
+    int s_models;                             // any label-noise model on
 };
 
 __host__ __device__ inline unsigned long long splitmix64_at(unsigned long long seed, unsigned long long i) {

@@ -64,6 +64,18 @@ struct RenderArgs {
     NoiseParams noise;
     unsigned long long* noise_frame;  // frame counter of the noise streams (advanced by every noisy launch)
     int prefetch_l2;     // stream every live scene's nodes and triangles into L2 at launch start
+    // Streamed download (may be null): page-locked host images [n][H][W] and
+    // [n][H][W][3] that receive each (agent, tile row) band of depth / rgb as
+    // soon as the band is complete; band_done[n][tiles_y] counts the band's
+    // completed tiles and tile_bits[n][tiles_y][tiles_x] the quarters of a tile
+    // rendered so far (both zero at launch start).  A tile can be rendered
+    // twice in a launch (a scheduled heavy tile also taken by the plain pass
+    // before its mark lands; both write the same values), so completion is
+    // recorded per tile, not by counting pixels.
+    float* host_depth = nullptr;
+    uint8_t* host_rgb = nullptr;
+    unsigned* band_done = nullptr;
+    unsigned* tile_bits = nullptr;
 };
 size_t render_smem_bytes(int warps_per_cta, int stack_depth, int rpl);
 int render_config_list(sim_render_config* out, int max);

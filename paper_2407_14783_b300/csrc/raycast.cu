@@ -109,10 +109,11 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
-// Noise draws of one pixel: 32 consecutive outputs of the generator starting
-// at ((frame * n_agents + agent) * H * W + pixel) * 32 (mod 2^64).  Slots: depth
-// 0-7, colour channel c 8 + 8c .. 15 + 8c, segmentation 30.  Within a block of 8:
-// Gaussian 0-1, speckle 2-3, shot 4-5, salt & pepper 6-7.
+// Noise draws of one pixel: 64 consecutive outputs of the generator starting
+// at ((frame * n_agents + agent) * H * W + pixel) * 64 (mod 2^64).  Slots: depth
+// 0-7, colour channel c 8 + 8c .. 15 + 8c, segmentation labels 32-39,
+// segmentation dropout 40.  Within a block of 8: Gaussian 0-1, speckle 2-3,
+// shot 4-5, salt & pepper 6-7.
 __device__ __forceinline__ float unit_open(unsigned long long x) {
     return ((float)(x >> 40) + 0.5f) * (1.0f / 16777216.0f);
 }
@@ -134,6 +135,18 @@ __device__ float noisy(float x, float hi, float gs, float sp, float shot, float 
     if (sandp > 0.0f && unit_half_open(splitmix64_at(seed, b + 6)) < sandp)
         x = unit_half_open(splitmix64_at(seed, b + 7)) < 0.5f ? 0.0f : hi;
     return fminf(fmaxf(x, 0.0f), hi);
+}
+
+// Warp-wide copy of `bytes` from device memory (read through L2, where other
+// warps' stores are visible after their fence) to host memory.
+__device__ __noinline__ void copy_out(const uint8_t* src, uint8_t* dst, size_t bytes, int lane) {
+    if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst) | bytes) & 15) == 0) {
+        const uint4* s = reinterpret_cast<const uint4*>(src);
+        uint4* d = reinterpret_cast<uint4*>(dst);
+        for (size_t i = lane; i < bytes / 16; i += 32) d[i] = __ldcg(s + i);
+    } else {
+        for (size_t i = lane; i < bytes; i += 32) dst[i] = __ldcg(src + i);
+    }
 }
 
 __device__ __forceinline__ float comp4(const float4& v, int s) { return s == 0 ? v.x : s == 1 ? v.y : s == 2 ? v.z : v.w; }
@@ -544,7 +557,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
             const NoiseParams& nz = A.noise;
             const unsigned long long nb =
                 ((noise_frame * (unsigned long long)A.n_agents + agent) * (unsigned long long)(H * W) +
-                 (unsigned long long)(pix_r[q] * W + pix_c[q])) * 32ull;
+                 (unsigned long long)(pix_r[q] * W + pix_c[q])) * 64ull;
             if (in && A.depth) {
                 float dv = ray[q].best_t;
                 if (nz.enabled) dv = noisy(dv, A.cam.max_depth, nz.d_gauss, nz.d_speckle, nz.d_shot, nz.d_sp, nz.seed, nb);
@@ -553,7 +566,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
             if (in && A.hit_id) A.hit_id[off] = ray[q].best_id;
             if (in && A.seg) {
                 int lab = ray[q].best_id >= 0 ? (row.labels ? __ldg(row.labels + ray[q].best_id) : ray[q].best_id) : -1;
-                if (nz.enabled && nz.s_sp > 0.0f && unit_half_open(splitmix64_at(nz.seed, nb + 30)) < nz.s_sp) lab = -1;
+                if (nz.enabled && nz.s_models && lab >= 0)
+                    lab = (int)rintf(noisy((float)lab, nz.s_max, nz.s_gauss, nz.s_speckle, nz.s_shot, nz.s_sp, nz.seed,
+                                           nb + 32));
+                if (nz.enabled && nz.s_drop > 0.0f && unit_half_open(splitmix64_at(nz.seed, nb + 40)) < nz.s_drop)
+                    lab = -1;
                 A.seg[off] = lab;
             }
             if (A.rgb) {
@@ -595,6 +612,31 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                 }
             }
             __syncwarp();
+        }
+        if (A.band_done) {
+            // Streamed download: the warp that completes an (agent, tile row)
+            // band copies it from the output buffers (just written, resident in
+            // L2) to the page-locked host images in 16-byte pieces, so the
+            // transfer over the bus runs during the rest of the ray cast.
+            __threadfence();  // this lane's image stores before the completion marks
+            __syncwarp();
+            const size_t band = (size_t)agent * tiles_y + ty;
+            unsigned last = 0;
+            if (lane == 0) {
+                const unsigned bits = sub < 0 ? (1u << kSplit) - 1u : 1u << sub;
+                const unsigned old = atomicOr(A.tile_bits + band * tiles_x + (tx0 / TW), bits);
+                if (old != (1u << kSplit) - 1u && (old | bits) == (1u << kSplit) - 1u)
+                    last = atomicAdd(A.band_done + band, 1u) + 1u == (unsigned)tiles_x;
+            }
+            if (__shfl_sync(kFull, last, 0)) {
+                __threadfence();
+                const int rows = min(TH, H - ty0);
+                const size_t first = frame + (size_t)ty0 * W, px = (size_t)rows * W;
+                if (A.host_depth && A.depth)
+                    copy_out(reinterpret_cast<const uint8_t*>(A.depth + first), reinterpret_cast<uint8_t*>(A.host_depth + first),
+                             4 * px, lane);
+                if (A.host_rgb && A.rgb) copy_out(A.rgb + 3 * first, A.host_rgb + 3 * first, 3 * px, lane);
+            }
         }
         if (COUNT) ++c_items;
         if (sched && lane == 0) {

@@ -7,7 +7,17 @@ pytestmark = pytest.mark.gpu
 
 NOISE = {"seed": 1234, "first_frame": 5, "depth_gauss": 0.02, "depth_speckle": 0.01, "depth_shot": 50.0,
          "depth_salt_pepper": 0.01, "rgb_gauss": 3.0, "rgb_speckle": 0.02, "rgb_shot": 0.5, "rgb_salt_pepper": 0.01,
-         "seg_dropout": 0.05}
+         "seg_dropout": 0.05, "seg_gauss": 0.8, "seg_speckle": 0.01, "seg_shot": 2.0, "seg_salt_pepper": 0.02,
+         "seg_max": 60}
+
+
+def _unrounded_labels(onoise, cfg, n, seg_clean):
+    """The oracle's segmentation labels after noise, before rounding (only the
+    boundary test needs them; misses and dropped pixels are far from .5)."""
+    H, W = seg_clean.shape[1:]
+    b = onoise.counter_base(cfg["first_frame"], n, np.arange(n), H, W)
+    return onoise._noisy(seg_clean.astype(np.float64), float(cfg["seg_max"]), cfg["seg_gauss"], cfg["seg_speckle"],
+                         cfg["seg_shot"], cfg["seg_salt_pepper"], cfg["seed"], b + np.uint64(onoise.SEG_BLOCK))
 
 
 def _setup(make_sim, wl):
@@ -67,7 +77,12 @@ def test_noise_matches_oracle_and_is_reproducible(make_sim, oracle_mod, wl):
     assert diff[clear].max() <= 1
     near = np.abs(cn - np.floor(cn) - 0.5) < 1e-3
     assert not np.any((diff == 1) & clear[..., None] & ~near)
-    assert np.array_equal(g1[clear], sn[clear])
+    # labels are rounded from a float as well: exact away from rounding
+    # boundaries of the unrounded oracle label, else at most one apart
+    su = _unrounded_labels(onoise, NOISE, n, seg_clean)
+    snear = np.abs(su - np.floor(su) - 0.5) < 1e-3
+    sdiff = np.abs(g1.astype(np.int64) - sn.astype(np.int64))
+    assert np.all(sdiff[clear & ~snear] == 0) and sdiff[clear].max() <= 1
     sim.set_noise(None)
     out = _render(sim, ids, st, n)
     for a, b in zip(out, (d0, c0, h0, g0)):
