@@ -8,15 +8,20 @@
 //
 // What it computes (paper sections and equations in brackets):
 //   * one control step of N quadrotors [Sec. III-A, Eq. 1-4]:
-//       body-rate (CTBR) controller -> rotor first-order lag [Eq. 4] ->
-//       thrust and moment [Eq. 3] -> RK4 (or Euler) on the rigid body [Eq. 1]
-//       with quadratic body-frame drag [Eq. 2] -> quaternion normalisation;
+//       controller (body rate CTBR, single-rotor thrust SRT, or geometric
+//       linear-velocity LV / position PS control after Lee et al.) ->
+//       rotor first-order lag [Eq. 4] -> thrust and moment [Eq. 3] -> RK4 (or
+//       Euler) on the rigid body [Eq. 1] with quadratic body-frame drag
+//       [Eq. 2] -> quaternion normalisation;
 //   * the closest-hit depth / colour / triangle-id image of every agent's
 //     pinhole camera over a triangle mesh [Sec. III-B] (Moller-Trumbore,
 //     brute force or a median-split BVH of its own);
 //   * exact forward-mode (dual number) derivatives of the step map and of a
 //     rollout loss, for checking the hand-written adjoint [Sec. III-A: the
-//     dynamics are differentiable].
+//     dynamics are differentiable];
+//   * the nearest point of a scene's mesh to each agent [Sec. III-B, the
+//     obstacle-distance module], by brute force over every triangle with
+//     Ericson's closest point on a triangle (Voronoi regions).
 //
 // Readings of points the paper leaves open (drag sign, moment-arm meaning,
 // frame layout, constants, camera convention, ties) are the ones listed in the
@@ -25,7 +30,9 @@
 // Parity: every function below is pinned by closed-form tests (hover
 // equilibrium, free fall, drag terminal velocity, rate-loop response, rotor
 // lag, constant-rate rotation, torque-free symmetric top, RK4 order, analytic
-// plane / box / sphere depths, brute force vs BVH, finite differences).
+// plane / box / sphere depths, brute force vs BVH, finite differences,
+// controller equilibria and step responses, rotation equivariance, box and
+// room distances).
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
