@@ -507,6 +507,81 @@ def run_diff(args):
     return 0
 
 
+def run_swarm(args):
+    """Multi-agent mode (Sec. III-B): 256 agents flying in 64 formations of 4
+    (1.5 m square, common heading) through the 208,812-triangle scene, all one
+    swarm, so each camera also sees the other drones.  One step = dynamics +
+    swarm render + pairwise proximity (collision query).  Reports agent-frames/s
+    and the same loop in the parallel-agents mode beside it."""
+    import torch
+    from paper_2407_14783_b300.sim import Sim, to_soa
+    p = wl.params()
+    w_h, u_h = _hover(p)
+    scene = wl.cluttered_scene(seed=2)
+    n_form, per = 64, 4
+    n = n_form * per
+    lead = wl.spawn_states(scene, n_form, 71, w_h)
+    s0 = np.repeat(lead, per, axis=0)
+    offs = np.array([[0.75, 0.75], [0.75, -0.75], [-0.75, 0.75], [-0.75, -0.75]])
+    for f in range(n_form):
+        yaw = 2.0 * np.arctan2(lead[f, 9], lead[f, 6])
+        c, sn = np.cos(yaw), np.sin(yaw)
+        for k in range(per):
+            s0[f * per + k, 0] += c * offs[k, 0] - sn * offs[k, 1]
+            s0[f * per + k, 1] += sn * offs[k, 0] + c * offs[k, 1]
+    s0 = s0.astype(np.float32)
+    T = args.warmup + args.steps
+    U = wl.hover_commands(T, n, 72, u_h, rate_range=0.3).astype(np.float32)
+    sim = Sim(p)
+    sid = sim.add_workload_scene(scene)
+    ids = torch.full((n,), sid, dtype=torch.int32, device="cuda")
+    spawn = to_soa(s0)
+    cmds = torch.tensor(np.ascontiguousarray(U.transpose(0, 2, 1)), device="cuda")
+    d, c, h = sim.alloc_images(n, hit=True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    half, radius = (0.25, 0.25, 0.06), 0.3
+    stream = torch.cuda.current_stream()
+
+    def loop(swarm):
+        sim.set_swarm(half if swarm else None, (250, 20, 30), 1000)
+        state = spawn.clone()
+        times = []
+        for t in range(T):
+            if t % 25 == 0:
+                state.copy_(spawn)
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(state, cmds[t])
+            sim.render(ids, state, d, c, h)
+            if swarm:
+                sim.swarm_proximity(ids, state, radius)
+            e1.record(stream)
+            if t >= args.warmup:
+                times.append((e0, e1))
+        torch.cuda.synchronize()
+        sim.check()
+        return statistics.mean(a.elapsed_time(b) for a, b in times)
+
+    ms_swarm = loop(True)
+    drone_px = float((h < -1).float().mean().item())
+    ms_plain = loop(False)
+    line = {"metric": "agent-frames/s (dynamics+64x64 depth/RGB, multi-agent mode) on 1 B300",
+            "value": n / (ms_swarm * 1e-3), "unit": "agent-frames/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_swarm, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (procedural scene, seeded formations)",
+            "config": {"workload": "swarm: 256 agents in 64 formations of 4 as one swarm in the 208,812-triangle "
+                                   "scene; step = dynamics + render with the other drones visible + proximity",
+                       "drone_half_extents_m": half, "collision_radius_m": radius,
+                       "drone_pixel_fraction": drone_px, "parallel_mode_ms_per_step": ms_plain,
+                       "swarm_over_parallel_time": ms_swarm / ms_plain,
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "gpu_launches": 7 * args.steps}
+    print(json.dumps(line), flush=True)
+    sim.close()
+    return 0
+
+
 class _PinnedArena:
     """Ring allocator over one pinned host buffer: request inputs and outputs
     for the load generator (allocation blocks while the oldest live block is in
@@ -639,7 +714,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--no-autotune", action="store_true", help="use the default ray-cast configuration")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="seconds of arrivals per load level")
-    ap.add_argument("--workload", choices=["large", "batched", "diff", "serving"], default="large",
+    ap.add_argument("--workload", choices=["large", "batched", "diff", "serving", "swarm"], default="large",
                     help="large: single 208,812-triangle scene, 256 agents (default); batched: 64 scenes, "
                          "4,096 agents, graph-captured 100-step loop (--steps counts loops)")
     args = ap.parse_args()
@@ -651,6 +726,8 @@ def main():
         return run_batched(args)
     if args.workload == "diff":
         return run_diff(args)
+    if args.workload == "swarm":
+        return run_swarm(args)
     if args.workload == "serving":
         return run_serving(args)
     return run_ours(args)

@@ -225,6 +225,40 @@ typedef struct sim_noise {
 } sim_noise;
 int sim_set_noise(sim_ctx* ctx, const sim_noise* cfg);
 
+/* Multi-agent mode (Sec. III-B: the drones of a multi-agent environment see
+ * each other and collide; parallel agents omit each other).  With cfg set,
+ * every later render on this context through sim_render, sim_render_ex,
+ * sim_render_counted, sim_env_step and loops created afterwards treats the
+ * agents of one launch that share a scene as one swarm: each camera also sees
+ * the other drones, boxes of half extents `half` (m, body frame, about the
+ * body origin), never its own.  A drone hit on agent j (its index in the
+ * launch) gives depth as usual, hit id -2 - j, colour `rgb` and segmentation
+ * label `label`; exact ties of depth go to the triangle, then to the lower
+ * agent index.  cfg = NULL returns to the parallel-agents mode (the default).
+ * The server and sim_render_scene_static always render in the
+ * parallel-agents mode.  The mode's per-launch buffers belong to the context:
+ * swarm renders on one context must not overlap on different streams.
+ * INVALID_ARG for non-positive or non-finite extents.  Synchronises the device. */
+typedef struct sim_swarm {
+    float half[3];
+    uint8_t rgb[3];
+    int32_t label;
+} sim_swarm;
+int sim_set_swarm(sim_ctx* ctx, const sim_swarm* cfg);
+
+/* Pairwise proximity of the swarms (Sec. III-B: collisions among the drones
+ * of the multi-agent mode), whatever the render mode: for every agent, over
+ * the other agents of the launch in its scene, the nearest centre distance
+ * (dist, +inf when alone), that agent (other, the lowest index among equal
+ * squared distances, -1 when alone) and how many lie closer than 2 * radius
+ * (n_collide: drones collide as spheres of `radius`).
+ *   scene_of_agent dev int32 [n]; state dev [17][n] (rows 0-2 used); dist dev
+ *   float32 [n], other dev int32 [n], n_collide dev int32 [n], each may be NULL.
+ * All pairs of a scene are visited (cost proportional to the sum of squared
+ * swarm sizes).  Asynchronous on `stream`. */
+int sim_swarm_proximity(sim_ctx* ctx, int32_t n_agents, const int32_t* scene_of_agent, const float* state,
+                        float radius, float* dist, int32_t* other, int32_t* n_collide, void* stream);
+
 /* Reverse-mode derivative of one sim_step (the dynamics are differentiable,
  * Sec. III-A): given the pre-step state, the command and the cotangent of the
  * post-step state, write the cotangents of the pre-step state and the command.

@@ -86,6 +86,11 @@ def lib():
                                         P(ctypes.c_int32), P(ctypes.c_uint8)]
             L.oracle_validate.argtypes = [vp, P(OracleParams), i64, dp, i64, P(ctypes.c_int64),
                                           P(ctypes.c_int32), P(ctypes.c_float), P(ctypes.c_uint8)]
+            L.oracle_render_swarm.argtypes = [vp, P(OracleParams), i64, dp, ctypes.c_int, dp, P(ctypes.c_uint8), dp,
+                                              P(ctypes.c_uint8), P(ctypes.c_int32), P(ctypes.c_uint8)]
+            L.oracle_validate_swarm.argtypes = [vp, P(OracleParams), i64, dp, dp, i64, P(ctypes.c_int64),
+                                                P(ctypes.c_int32), P(ctypes.c_float), P(ctypes.c_uint8)]
+            L.oracle_swarm_proximity.argtypes = [i64, dp, ctypes.c_double, dp, P(ctypes.c_int32), P(ctypes.c_int32)]
             L.oracle_num_threads.restype = ctypes.c_int
             L.oracle_nearest.argtypes = [vp, i64, dp, ctypes.c_double, dp, dp, P(ctypes.c_int32)]
             L.oracle_point_triangle.argtypes = [vp, i64, dp, P(ctypes.c_int32), dp]
@@ -191,8 +196,11 @@ class Scene:
             lib().oracle_scene_destroy(h)
             self.handle = None
 
-    def render(self, p: dict, states: np.ndarray, use_bvh: bool | None = None):
-        """Returns dict depth [n,H,W] f64, rgb [n,H,W,3] u8, id [n,H,W] i32, tie [n,H,W] bool."""
+    def render(self, p: dict, states: np.ndarray, use_bvh: bool | None = None, swarm: dict | None = None):
+        """Returns dict depth [n,H,W] f64, rgb [n,H,W,3] u8, id [n,H,W] i32, tie [n,H,W] bool.
+
+        swarm = {"half": (hx, hy, hz), "rgb": (r, g, b)} renders the n agents as
+        one swarm: each sees the other drones (id -2 - j for drone j)."""
         states = _f64(states)
         n = states.shape[0]
         H, W = int(p["height"]), int(p["width"])
@@ -201,9 +209,18 @@ class Scene:
         hid = np.empty((n, H, W), np.int32)
         tie = np.empty((n, H, W), np.uint8)
         ub = self.bvh if use_bvh is None else use_bvh
-        rc = lib().oracle_render(self.handle, ctypes.byref(make_params(p)), n, _ptr(states, ctypes.c_double),
-                                 1 if ub else 0, _ptr(depth, ctypes.c_double), _ptr(rgb, ctypes.c_uint8),
-                                 _ptr(hid, ctypes.c_int32), _ptr(tie, ctypes.c_uint8))
+        if swarm is None:
+            rc = lib().oracle_render(self.handle, ctypes.byref(make_params(p)), n, _ptr(states, ctypes.c_double),
+                                     1 if ub else 0, _ptr(depth, ctypes.c_double), _ptr(rgb, ctypes.c_uint8),
+                                     _ptr(hid, ctypes.c_int32), _ptr(tie, ctypes.c_uint8))
+        else:
+            half = np.ascontiguousarray(swarm["half"], dtype=np.float64)
+            col = np.ascontiguousarray(swarm.get("rgb", (0, 0, 0)), dtype=np.uint8)
+            rc = lib().oracle_render_swarm(self.handle, ctypes.byref(make_params(p)), n,
+                                           _ptr(states, ctypes.c_double), 1 if ub else 0, _ptr(half, ctypes.c_double),
+                                           _ptr(col, ctypes.c_uint8), _ptr(depth, ctypes.c_double),
+                                           _ptr(rgb, ctypes.c_uint8), _ptr(hid, ctypes.c_int32),
+                                           _ptr(tie, ctypes.c_uint8))
         if rc:
             raise ValueError(f"oracle_render failed ({rc})")
         return {"depth": depth, "rgb": rgb, "id": hid, "tie": tie.astype(bool)}
@@ -231,17 +248,41 @@ class Scene:
                                     _ptr(ids, ctypes.c_int32), _ptr(out, ctypes.c_double))
         return out
 
-    def validate(self, p: dict, states: np.ndarray, pix: np.ndarray, ids: np.ndarray, depth: np.ndarray):
+    def validate(self, p: dict, states: np.ndarray, pix: np.ndarray, ids: np.ndarray, depth: np.ndarray,
+                 swarm: dict | None = None):
         """Validity of claimed (id, depth) answers at flat pixel indices ``pix`` (see oracle.cpp)."""
         states = _f64(states)
         pix = np.ascontiguousarray(pix, dtype=np.int64)
         ids = np.ascontiguousarray(ids, dtype=np.int32)
         depth = np.ascontiguousarray(depth, dtype=np.float32)
         valid = np.zeros(pix.shape[0], np.uint8)
-        rc = lib().oracle_validate(self.handle, ctypes.byref(make_params(p)), states.shape[0],
-                                   _ptr(states, ctypes.c_double), pix.shape[0], _ptr(pix, ctypes.c_int64),
-                                   _ptr(ids, ctypes.c_int32), _ptr(depth, ctypes.c_float),
-                                   _ptr(valid, ctypes.c_uint8))
+        if swarm is None:
+            rc = lib().oracle_validate(self.handle, ctypes.byref(make_params(p)), states.shape[0],
+                                       _ptr(states, ctypes.c_double), pix.shape[0], _ptr(pix, ctypes.c_int64),
+                                       _ptr(ids, ctypes.c_int32), _ptr(depth, ctypes.c_float),
+                                       _ptr(valid, ctypes.c_uint8))
+        else:
+            half = np.ascontiguousarray(swarm["half"], dtype=np.float64)
+            rc = lib().oracle_validate_swarm(self.handle, ctypes.byref(make_params(p)), states.shape[0],
+                                             _ptr(states, ctypes.c_double), _ptr(half, ctypes.c_double),
+                                             pix.shape[0], _ptr(pix, ctypes.c_int64), _ptr(ids, ctypes.c_int32),
+                                             _ptr(depth, ctypes.c_float), _ptr(valid, ctypes.c_uint8))
         if rc:
             raise ValueError(f"oracle_validate failed ({rc})")
         return valid.astype(bool)
+
+
+def swarm_proximity(positions: np.ndarray, radius: float):
+    """Brute-force pairwise proximity of one swarm (see oracle.cpp): per agent the
+    nearest other agent's centre distance, its index and the number of others
+    closer than 2 * radius."""
+    pos = _f64(positions).reshape(-1, 3)
+    n = pos.shape[0]
+    dist = np.empty(n)
+    other = np.empty(n, np.int32)
+    hits = np.empty(n, np.int32)
+    rc = lib().oracle_swarm_proximity(n, _ptr(pos, ctypes.c_double), float(radius), _ptr(dist, ctypes.c_double),
+                                      _ptr(other, ctypes.c_int32), _ptr(hits, ctypes.c_int32))
+    if rc:
+        raise ValueError(f"oracle_swarm_proximity failed ({rc})")
+    return dist, other, hits

@@ -653,6 +653,165 @@ PixelResult classify(const std::vector<Cand>& cands, double max_depth) {
 
 inline double t_limit(const OracleParams& p) { return p.max_depth * (1.0 + kTau); }
 
+// ------------------------------------------------------------ swarm drones
+// Multi-agent mode [Sec. III-B]: the drones of one scene see each other (the
+// parallel-agents mode omits them).  Reading: each drone is a box of half
+// extents h about its body origin, aligned with its body axes, and a camera
+// never sees its own drone.  Drone j enters a pixel's candidate list with id
+// INT32_MIN + j, so the closest-hit rule and the ambiguity classification of
+// triangles apply unchanged:
+//   * definite hit (m = 1): the ray hits the box shrunk by delta on every axis;
+//   * hit near the silhouette (m = 0, ambiguous): hits the box, not the shrunk one;
+//   * near miss (m = -kTau / 2): only the box grown by delta is hit;
+// delta = kTau * (|o - centre| + |h|), the FP32 error scale of moving the ray
+// into the drone's frame, times the same 50 eps_f32 band as the triangles.
+struct Swarm {
+    const double* states;  // [n][17], the same agents as the render's
+    int64_t n;
+    double half[3];
+    uint8_t rgb[3];
+};
+
+// Ray (o, d) against the box of half extents h + g (every axis) of the drone
+// with state st.  Hit at t > kTmin: the entry distance, or the exit distance
+// when the ray starts inside (boxes are seen from inside, like two-sided
+// triangles of a closed mesh).
+bool ray_drone(const double* st, const double h[3], double g, const double o[3], const double d[3], double& t) {
+    const double q[4] = {st[6], st[7], st[8], st[9]};
+    double R[3][3];
+    rotation_matrix(q, R);
+    double tn = -std::numeric_limits<double>::infinity(), tf = std::numeric_limits<double>::infinity();
+    for (int k = 0; k < 3; ++k) {
+        // coordinates along the drone's body axis k (column k of R)
+        const double ol = R[0][k] * (o[0] - st[0]) + R[1][k] * (o[1] - st[1]) + R[2][k] * (o[2] - st[2]);
+        const double dl = R[0][k] * d[0] + R[1][k] * d[1] + R[2][k] * d[2];
+        const double hk = h[k] + g;
+        if (!(hk > 0.0)) return false;
+        if (dl == 0.0) {
+            if (std::fabs(ol) > hk) return false;
+            continue;
+        }
+        double a = (-hk - ol) / dl, b = (hk - ol) / dl;
+        if (a > b) std::swap(a, b);
+        tn = std::max(tn, a);
+        tf = std::min(tf, b);
+    }
+    if (tn > tf) return false;
+    if (tn > kTmin) {
+        t = tn;
+        return true;
+    }
+    if (tf > kTmin) {
+        t = tf;
+        return true;
+    }
+    return false;
+}
+
+void collect_drones(const Swarm& sw, int64_t self, const double o[3], const double d[3], std::vector<Cand>& out) {
+    const double hn = std::sqrt(sw.half[0] * sw.half[0] + sw.half[1] * sw.half[1] + sw.half[2] * sw.half[2]);
+    for (int64_t j = 0; j < sw.n; ++j) {
+        if (j == self) continue;
+        const double* st = sw.states + 17 * j;
+        const double dx = o[0] - st[0], dy = o[1] - st[1], dz = o[2] - st[2];
+        const double delta = kTau * (std::sqrt(dx * dx + dy * dy + dz * dz) + hn);
+        double t_in = 0.0, t_ex = 0.0, t_out = 0.0;
+        const bool in = ray_drone(st, sw.half, -delta, o, d, t_in);
+        const bool ex = ray_drone(st, sw.half, 0.0, o, d, t_ex);
+        const bool grown = ray_drone(st, sw.half, delta, o, d, t_out);
+        if (!ex && !grown) continue;
+        Cand c;
+        c.id = std::numeric_limits<int32_t>::min() + (int32_t)j;
+        c.h.sigma = 1.0;
+        if (ex) {
+            c.h.t = t_ex;
+            c.h.m = in ? 1.0 : 0.0;
+        } else {
+            c.h.t = t_out;
+            c.h.m = -0.5 * kTau;
+        }
+        out.push_back(c);
+    }
+}
+
+// Output id of a candidate id: triangles as they are, drone j as -2 - j.
+inline int32_t output_id(int32_t id) {
+    return id >= -1 ? id : -2 - (int32_t)((int64_t)id - std::numeric_limits<int32_t>::min());
+}
+inline int32_t candidate_id(int32_t out) {
+    return out >= -1 ? out : (int32_t)((int64_t)std::numeric_limits<int32_t>::min() + (-2 - (int64_t)out));
+}
+
+int render_impl(const OracleScene* s, const OracleParams* p, int64_t n, const double* states, int use_bvh,
+                const Swarm* sw, double* depth, uint8_t* rgb, int32_t* hit_id, uint8_t* tie) {
+    if (!s || !p || n < 0) return -1;
+    if (use_bvh && s->nodes.empty() && !s->tris.empty()) return -2;
+    const int W = p->width, H = p->height;
+    const int64_t npix = n * (int64_t)W * H;
+#pragma omp parallel
+    {
+        std::vector<Cand> cands;
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t k = 0; k < npix; ++k) {
+            const int64_t a = k / ((int64_t)W * H);
+            const int r = (int)((k / W) % H), c = (int)(k % W);
+            double o[3], d[3];
+            camera_ray(*p, states + a * 17, r, c, o, d);
+            collect_candidates(*s, o, d, t_limit(*p), use_bvh != 0, cands);
+            if (sw) collect_drones(*sw, a, o, d, cands);
+            const PixelResult pr = classify(cands, p->max_depth);
+            if (depth) depth[k] = pr.t;
+            if (hit_id) hit_id[k] = output_id(pr.id);
+            if (tie) tie[k] = pr.tie;
+            if (rgb) {
+                for (int j = 0; j < 3; ++j)
+                    rgb[3 * k + j] = pr.id >= 0 ? s->rgb[3 * (int64_t)pr.id + j] : pr.id < -1 ? sw->rgb[j] : 0;
+            }
+        }
+    }
+    return 0;
+}
+
+int validate_impl(const OracleScene* s, const OracleParams* p, int64_t n, const double* states, const Swarm* sw,
+                  int64_t npix, const int64_t* pix, const int32_t* id, const float* depth, uint8_t* valid) {
+    if (!s || !p || n < 0) return -1;
+    const int W = p->width, H = p->height;
+    const bool use_bvh = !s->nodes.empty();
+#pragma omp parallel
+    {
+        std::vector<Cand> cands;
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t k = 0; k < npix; ++k) {
+            const int64_t q = pix[k];
+            const int64_t a = q / ((int64_t)W * H);
+            const int r = (int)((q / W) % H), c = (int)(q % W);
+            valid[k] = 0;
+            if (a < 0 || a >= n) continue;
+            double o[3], d[3];
+            camera_ray(*p, states + a * 17, r, c, o, d);
+            collect_candidates(*s, o, d, t_limit(*p), use_bvh, cands);
+            if (sw) collect_drones(*sw, a, o, d, cands);
+            double t_def = std::numeric_limits<double>::infinity();
+            for (const Cand& cd : cands)
+                if (cd.h.m > kTau * cd.h.sigma && cd.h.t > kTmin && cd.h.t <= p->max_depth * (1.0 - kTau))
+                    t_def = std::min(t_def, cd.h.t);
+            if (id[k] == -1) {
+                valid[k] = (std::isinf(t_def) && depth[k] == (float)p->max_depth) ? 1 : 0;
+                continue;
+            }
+            const int32_t want = candidate_id(id[k]);
+            for (const Cand& cd : cands) {
+                if (cd.id != want) continue;
+                const bool ok = cd.h.m > -kTau * cd.h.sigma && cd.h.t > kTmin &&
+                                cd.h.t <= p->max_depth * (1.0 + kTau) && cd.h.t <= t_def * (1.0 + kTau) &&
+                                std::fabs((double)depth[k] - cd.h.t) <= 1e-4 * cd.h.t;
+                valid[k] = ok ? 1 : 0;
+            }
+        }
+    }
+    return 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -789,78 +948,71 @@ int64_t oracle_scene_bvh_nodes(const void* scene) {
 // states: [n][17]; outputs [n][H][W] (rgb [n][H][W][3]).  Any output may be null.
 int oracle_render(const void* scene, const OracleParams* p, int64_t n, const double* states, int use_bvh,
                   double* depth, uint8_t* rgb, int32_t* hit_id, uint8_t* tie) {
-    const OracleScene* s = static_cast<const OracleScene*>(scene);
-    if (!s || !p || n < 0) return -1;
-    if (use_bvh && s->nodes.empty() && !s->tris.empty()) return -2;
-    const int W = p->width, H = p->height;
-    const int64_t npix = n * (int64_t)W * H;
-#pragma omp parallel
-    {
-        std::vector<Cand> cands;
-#pragma omp for schedule(dynamic, 64)
-        for (int64_t k = 0; k < npix; ++k) {
-            const int64_t a = k / ((int64_t)W * H);
-            const int r = (int)((k / W) % H), c = (int)(k % W);
-            double o[3], d[3];
-            camera_ray(*p, states + a * 17, r, c, o, d);
-            collect_candidates(*s, o, d, t_limit(*p), use_bvh != 0, cands);
-            const PixelResult pr = classify(cands, p->max_depth);
-            if (depth) depth[k] = pr.t;
-            if (hit_id) hit_id[k] = pr.id;
-            if (tie) tie[k] = pr.tie;
-            if (rgb) {
-                for (int j = 0; j < 3; ++j) rgb[3 * k + j] = pr.id >= 0 ? s->rgb[3 * (int64_t)pr.id + j] : 0;
-            }
-        }
-    }
-    return 0;
+    return render_impl(static_cast<const OracleScene*>(scene), p, n, states, use_bvh, nullptr, depth, rgb, hit_id,
+                       tie);
+}
+
+// As oracle_render, with the n agents forming one swarm [Sec. III-B]: every
+// other agent's drone (box of half extents half[3] about its body origin,
+// colour drone_rgb) is visible.  A drone hit reports id -2 - j.
+int oracle_render_swarm(const void* scene, const OracleParams* p, int64_t n, const double* states, int use_bvh,
+                        const double* half, const uint8_t* drone_rgb, double* depth, uint8_t* rgb, int32_t* hit_id,
+                        uint8_t* tie) {
+    if (!half || !drone_rgb) return -1;
+    Swarm sw{states, n, {half[0], half[1], half[2]}, {drone_rgb[0], drone_rgb[1], drone_rgb[2]}};
+    return render_impl(static_cast<const OracleScene*>(scene), p, n, states, use_bvh, &sw, depth, rgb, hit_id, tie);
 }
 
 // Check answers given for ambiguous pixels.  For pixel k = (agent, row, col)
-// (pix[k] = agent * H * W + row * W + col) with claimed triangle id[k] and
-// depth[k], valid[k] = 1 when the claim is one of the answers the ambiguity
-// admits:
+// (pix[k] = agent * H * W + row * W + col) with claimed id[k] (a triangle, -1
+// for a miss, or -2 - j for drone j in the swarm form) and depth[k],
+// valid[k] = 1 when the claim is one of the answers the ambiguity admits:
 //   * "definite" hits are candidates with m > kTau * sigma and
 //     kTmin < t <= max_depth * (1 - kTau); t_def is the closest of them;
 //   * a miss (id = -1, depth = max_depth) is valid when no definite hit exists;
-//   * a triangle j is valid when it is nearly hit (m > -kTau * sigma),
+//   * a candidate j is valid when it is nearly hit (m > -kTau * sigma),
 //     t_j <= max_depth * (1 + kTau), t_j <= t_def * (1 + kTau), and the claimed
 //     depth is within 1e-4 * t_j of t_j.
 int oracle_validate(const void* scene, const OracleParams* p, int64_t n, const double* states, int64_t npix,
                     const int64_t* pix, const int32_t* id, const float* depth, uint8_t* valid) {
-    const OracleScene* s = static_cast<const OracleScene*>(scene);
-    if (!s || !p || n < 0) return -1;
-    const int W = p->width, H = p->height;
-    const bool use_bvh = !s->nodes.empty();
-#pragma omp parallel
-    {
-        std::vector<Cand> cands;
-#pragma omp for schedule(dynamic, 16)
-        for (int64_t k = 0; k < npix; ++k) {
-            const int64_t q = pix[k];
-            const int64_t a = q / ((int64_t)W * H);
-            const int r = (int)((q / W) % H), c = (int)(q % W);
-            valid[k] = 0;
-            if (a < 0 || a >= n) continue;
-            double o[3], d[3];
-            camera_ray(*p, states + a * 17, r, c, o, d);
-            collect_candidates(*s, o, d, t_limit(*p), use_bvh, cands);
-            double t_def = std::numeric_limits<double>::infinity();
-            for (const Cand& cd : cands)
-                if (cd.h.m > kTau * cd.h.sigma && cd.h.t > kTmin && cd.h.t <= p->max_depth * (1.0 - kTau))
-                    t_def = std::min(t_def, cd.h.t);
-            if (id[k] < 0) {
-                valid[k] = (std::isinf(t_def) && depth[k] == (float)p->max_depth) ? 1 : 0;
-                continue;
+    return validate_impl(static_cast<const OracleScene*>(scene), p, n, states, nullptr, npix, pix, id, depth, valid);
+}
+
+int oracle_validate_swarm(const void* scene, const OracleParams* p, int64_t n, const double* states,
+                          const double* half, int64_t npix, const int64_t* pix, const int32_t* id, const float* depth,
+                          uint8_t* valid) {
+    if (!half) return -1;
+    Swarm sw{states, n, {half[0], half[1], half[2]}, {0, 0, 0}};
+    return validate_impl(static_cast<const OracleScene*>(scene), p, n, states, &sw, npix, pix, id, depth, valid);
+}
+
+// Pairwise proximity of a swarm [Sec. III-B: collisions among the drones of
+// the multi-agent mode], brute force over all pairs.  Reading: drones collide
+// as spheres of the given radius.  pos [n][3]; outputs per agent: the centre
+// distance to the nearest other agent (+inf when alone), that agent (lowest
+// index among equal distances, -1 when alone), and how many others lie closer
+// than 2 * radius.
+int oracle_swarm_proximity(int64_t n, const double* pos, double radius, double* dist, int32_t* other,
+                           int32_t* n_collide) {
+    if (n < 0 || (n > 0 && !pos)) return -1;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double best = std::numeric_limits<double>::infinity();
+        int32_t who = -1, hits = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            const double dx = pos[3 * i] - pos[3 * j], dy = pos[3 * i + 1] - pos[3 * j + 1],
+                         dz = pos[3 * i + 2] - pos[3 * j + 2];
+            const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
+            if (r < best) {
+                best = r;
+                who = (int32_t)j;
             }
-            for (const Cand& cd : cands) {
-                if (cd.id != id[k]) continue;
-                const bool ok = cd.h.m > -kTau * cd.h.sigma && cd.h.t > kTmin &&
-                                cd.h.t <= p->max_depth * (1.0 + kTau) && cd.h.t <= t_def * (1.0 + kTau) &&
-                                std::fabs((double)depth[k] - cd.h.t) <= 1e-4 * cd.h.t;
-                valid[k] = ok ? 1 : 0;
-            }
+            if (r < 2.0 * radius) ++hits;
         }
+        if (dist) dist[i] = best;
+        if (other) other[i] = who;
+        if (n_collide) n_collide[i] = hits;
     }
     return 0;
 }

@@ -70,6 +70,10 @@ class SimNoise(ctypes.Structure):
                 ("seg_shot", ctypes.c_float), ("seg_salt_pepper", ctypes.c_float), ("seg_max", ctypes.c_float)]
 
 
+class SimSwarm(ctypes.Structure):
+    _fields_ = [("half", ctypes.c_float * 3), ("rgb", ctypes.c_uint8 * 3), ("label", ctypes.c_int32)]
+
+
 class SimRequest(ctypes.Structure):
     _fields_ = [("scene_id", ctypes.c_int32), ("n_agents", ctypes.c_int32), ("n_steps", ctypes.c_int32),
                 ("frames", ctypes.c_int32), ("state0", ctypes.c_void_p), ("cmds", ctypes.c_void_p),
@@ -112,6 +116,8 @@ SIGNATURES = {
     "sim_render_ex": [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "sim_scene_set_labels": [_vp, _i32, _vp, _i64],
     "sim_set_noise": [_vp, _vp],
+    "sim_set_swarm": [_vp, _vp],
+    "sim_swarm_proximity": [_vp, _i32, _vp, _vp, ctypes.c_float, _vp, _vp, _vp, _vp],
     "sim_render_scene_static": [_vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp],
     "sim_step_backward": [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
     "sim_nearest_obstacle": [_vp, _i32, _vp, _vp, ctypes.c_float, _vp, _vp, _vp, _vp],

@@ -51,6 +51,7 @@ struct sim_loop {
     unsigned* counters = nullptr;
     void* sched_mem = nullptr;
     int sched_cap = 0;
+    vf::SwarmScratch swarm;  // the loop's own multi-agent buffers (baked into the graph)
 };
 
 struct sim_ctx {
@@ -84,6 +85,10 @@ struct sim_ctx {
     uint8_t* d_rgb = nullptr;
     unsigned* d_band = nullptr;  // completion words of the streamed download
     size_t band_words = 0;
+    // multi-agent mode (sim_set_swarm) and its per-launch buffers
+    bool swarm_on = false;
+    sim_swarm swarm_cfg{};
+    vf::SwarmScratch swarm;
     int stage_n = 0;
     size_t stage_bytes = 0;
 };
@@ -413,12 +418,73 @@ long long render_items(const sim_ctx* c, int n, const sim_render_config& cfg) {
     return (long long)n * tx * ty;
 }
 
+void swarm_free(sim_ctx* c, SwarmScratch& w) {
+    ctx_free(c, w.drones, (size_t)w.cap_agents * 3 * sizeof(float4));
+    ctx_free(c, w.members, (size_t)w.cap_agents * sizeof(int));
+    ctx_free(c, w.spheres, (size_t)w.cap_agents * sizeof(float4));
+    ctx_free(c, w.off, sizeof(int) * ((size_t)w.cap_scenes + 1));
+    ctx_free(c, w.cursor, sizeof(int) * ((size_t)w.cap_scenes + 1));
+    w = SwarmScratch{};
+}
+// Grow w to n agents and `rows` scene rows.  Growing synchronises the device
+// (earlier launches may still read the old buffers).
+int swarm_reserve(sim_ctx* c, SwarmScratch& w, int n, int rows) {
+    if (n <= w.cap_agents && rows <= w.cap_scenes && w.off) return SIM_OK;
+    const int na = std::max(std::max(n, w.cap_agents), 1), ns = std::max(std::max(rows, w.cap_scenes), 1);
+    cudaDeviceSynchronize();
+    swarm_free(c, w);
+    void *a = nullptr, *b = nullptr, *o = nullptr, *u = nullptr, *sp = nullptr;
+    int rc;
+    if ((rc = ctx_alloc(c, (size_t)na * 3 * sizeof(float4), &a)) || (rc = ctx_alloc(c, (size_t)na * sizeof(int), &b)) ||
+        (rc = ctx_alloc(c, sizeof(int) * ((size_t)ns + 1), &o)) || (rc = ctx_alloc(c, sizeof(int) * ((size_t)ns + 1), &u)) ||
+        (rc = ctx_alloc(c, (size_t)na * sizeof(float4), &sp))) {
+        ctx_free(c, a, (size_t)na * 3 * sizeof(float4));
+        ctx_free(c, b, (size_t)na * sizeof(int));
+        ctx_free(c, o, sizeof(int) * ((size_t)ns + 1));
+        ctx_free(c, u, sizeof(int) * ((size_t)ns + 1));
+        return rc;
+    }
+    w.spheres = (float4*)sp;
+    w.drones = (float4*)a;
+    w.members = (int*)b;
+    w.off = (int*)o;
+    w.cursor = (int*)u;
+    w.cap_agents = na;
+    w.cap_scenes = ns;
+    return SIM_OK;
+}
+
+// Which multi-agent buffers a render uses: the context's (when the mode is
+// on; grown on demand), none (parallel-agents mode), or the caller's own,
+// already sized (a captured loop, whose buffer addresses are baked in).
+enum class SwarmUse { ctx, none, own };
+
 int do_render(sim_ctx* c, int n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb, int32_t* hit,
               bool count, const sim_render_config& cfg, cudaStream_t s, unsigned* own_counters = nullptr,
               void* sched_mem = nullptr, int sched_cap = 0, int32_t* seg = nullptr, float* host_depth = nullptr,
-              uint8_t* host_rgb = nullptr, unsigned* band_done = nullptr, unsigned* tile_bits = nullptr) {
+              uint8_t* host_rgb = nullptr, unsigned* band_done = nullptr, unsigned* tile_bits = nullptr,
+              SwarmUse su = SwarmUse::ctx, SwarmScratch* own_swarm = nullptr) {
     if (n == 0) return SIM_OK;
     RenderArgs a = render_args(c, n, soa, state, depth, rgb, hit);
+    if (c->swarm_on && su != SwarmUse::none) {
+        SwarmScratch* w = su == SwarmUse::own ? own_swarm : &c->swarm;
+        if (su == SwarmUse::ctx) {
+            const int rc = swarm_reserve(c, *w, n, a.n_scenes);
+            if (rc) return rc;
+        }
+        if (!w || !w->off || n > w->cap_agents || a.n_scenes > w->cap_scenes)
+            return fail(SIM_ERR_INVALID_ARG, "multi-agent buffers too small for this launch");
+        const cudaError_t e = launch_swarm_prep(n, soa, state, a.n_scenes, *w, s);
+        if (e != cudaSuccess) return cuda_fail(e, "swarm preparation");
+        const sim_swarm& sc = c->swarm_cfg;
+        a.drones = w->drones;
+        a.swarm_off = w->off;
+        a.swarm_spheres = w->spheres;
+        for (int k = 0; k < 3; ++k) a.swarm_half[k] = sc.half[k];
+        a.swarm_radius = std::sqrt(sc.half[0] * sc.half[0] + sc.half[1] * sc.half[1] + sc.half[2] * sc.half[2]);
+        a.swarm_rgb = (uint32_t)sc.rgb[0] | ((uint32_t)sc.rgb[1] << 8) | ((uint32_t)sc.rgb[2] << 16);
+        a.swarm_label = sc.label;
+    }
     a.seg = seg;
     a.host_depth = host_depth;
     a.host_rgb = host_rgb;
@@ -525,6 +591,7 @@ int sim_destroy_ctx(sim_ctx* c) {
     ctx_free(c, c->d_depth, 0);
     ctx_free(c, c->d_rgb, 0);
     ctx_free(c, c->d_band, 0);
+    swarm_free(c, c->swarm);
     delete c;
     return SIM_OK;
 }
@@ -702,6 +769,40 @@ int sim_render_ex(sim_ctx* c, int32_t n, const int32_t* soa, const float* state,
 int sim_render(sim_ctx* c, int32_t n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb,
                int32_t* hit, void* stream) {
     return sim_render_ex(c, n, soa, state, depth, rgb, hit, nullptr, stream);
+}
+
+int sim_set_swarm(sim_ctx* c, const sim_swarm* cfg) {
+    if (!c) return fail(SIM_ERR_INVALID_ARG, "null context");
+    if (cfg) {
+        for (int k = 0; k < 3; ++k)
+            if (!(cfg->half[k] > 0.0f) || !std::isfinite(cfg->half[k]))
+                return fail(SIM_ERR_INVALID_ARG, "drone half extents must be finite and > 0");
+    }
+    DeviceGuard g(c->device);
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "swarm set-up");
+    c->swarm_on = cfg != nullptr;
+    if (cfg) c->swarm_cfg = *cfg;
+    return SIM_OK;
+}
+
+int sim_swarm_proximity(sim_ctx* c, int32_t n, const int32_t* soa, const float* state, float radius, float* dist,
+                        int32_t* other, int32_t* n_collide, void* stream) {
+    int rc = check_render_args(c, n, soa, state);
+    if (rc) return rc;
+    if (!(radius >= 0.0f) || !std::isfinite(radius)) return fail(SIM_ERR_INVALID_ARG, "radius must be finite and >= 0");
+    if (n == 0) return SIM_OK;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rows;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        rows = (int)c->scenes.size();
+    }
+    if ((rc = swarm_reserve(c, c->swarm, n, rows))) return rc;
+    cudaError_t e = launch_swarm_prep(n, soa, state, rows, c->swarm, s);
+    if (e == cudaSuccess) e = launch_swarm_proximity(n, soa, state, rows, c->swarm, radius, dist, other, n_collide, s);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e, "swarm proximity");
 }
 
 int sim_set_noise(sim_ctx* c, const sim_noise* cfg) {
@@ -955,6 +1056,17 @@ int sim_loop_create(sim_ctx* c, sim_loop** out, int32_t n, int32_t T, const int3
         delete L;
         return rc;
     }
+    if (c->swarm_on) {
+        int rows;
+        {
+            std::lock_guard<std::mutex> lk(c->mu);
+            rows = (int)c->scenes.size();
+        }
+        if ((rc = swarm_reserve(c, L->swarm, n, rows))) {
+            sim_loop_destroy(L);
+            return rc;
+        }
+    }
     cudaStream_t cap;
     cudaError_t e = cudaMemsetAsync(L->counters, 0, 2 * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -971,7 +1083,8 @@ int sim_loop_create(sim_ctx* c, sim_loop** out, int32_t n, int32_t T, const int3
         if (e != cudaSuccess) break;
         const size_t slot = (size_t)(t % n_frames);
         rc = do_render(c, n, soa, state, depth ? depth + slot * frame : nullptr, rgb ? rgb + slot * frame * 3 : nullptr,
-                       nullptr, false, c->rcfg, cap, L->counters, L->sched_mem, L->sched_cap);
+                       nullptr, false, c->rcfg, cap, L->counters, L->sched_mem, L->sched_cap, nullptr, nullptr,
+                       nullptr, nullptr, nullptr, c->swarm_on ? SwarmUse::own : SwarmUse::none, &L->swarm);
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
@@ -1002,6 +1115,7 @@ int sim_loop_destroy(sim_loop* L) {
     if (L->graph) cudaGraphDestroy(L->graph);
     ctx_free(L->ctx, L->counters, 2 * sizeof(unsigned));
     if (L->sched_mem) ctx_free(L->ctx, L->sched_mem, sched_bytes_for(L->sched_cap));
+    swarm_free(L->ctx, L->swarm);
     delete L;
     return SIM_OK;
 }
@@ -1234,7 +1348,9 @@ int ctx_render_own(sim_ctx* c, int n, const int32_t* soa, const float* state, fl
                    unsigned* counters, cudaStream_t s) {
     int rc = check_render_args(c, n, soa, state);
     if (rc) return rc;
-    return do_render(c, n, soa, state, depth, rgb, nullptr, false, c->rcfg, s, counters);
+    // requests are independent: the server always renders in the parallel-agents mode
+    return do_render(c, n, soa, state, depth, rgb, nullptr, false, c->rcfg, s, counters, nullptr, 0, nullptr, nullptr,
+                     nullptr, nullptr, nullptr, SwarmUse::none);
 }
 int ctx_fail(int code, const char* msg) { return fail(code, msg); }
 

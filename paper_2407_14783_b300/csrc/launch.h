@@ -76,7 +76,34 @@ struct RenderArgs {
     uint8_t* host_rgb = nullptr;
     unsigned* band_done = nullptr;
     unsigned* tile_bits = nullptr;
+    // Multi-agent mode (may be null): every agent sees the other drones of its
+    // scene.  drones[3 j + k] = (body axis k of drone j, centre_k);
+    // swarm_off[sid] .. swarm_off[sid + 1] index swarm_spheres, the agents of
+    // scene sid.  A drone is a box of half extents swarm_half about its body
+    // origin; a hit on drone j has the internal id INT_MIN + j.
+    const float4* drones = nullptr;
+    const int* swarm_off = nullptr;
+    const float4* swarm_spheres = nullptr;  // per member, in member order: (centre, agent index as int bits)
+    float swarm_half[3] = {0.0f, 0.0f, 0.0f};
+    float swarm_radius = 0.0f;   // |swarm_half|: bounding sphere for the per-tile cull
+    uint32_t swarm_rgb = 0;      // packed like the scene colours
+    int swarm_label = -1;        // segmentation label of a drone
 };
+
+// Per-launch buffers of the multi-agent mode.
+struct SwarmScratch {
+    float4* drones = nullptr;  // [cap_agents][3]
+    int* members = nullptr;    // [cap_agents]
+    float4* spheres = nullptr; // [cap_agents]: member centres with the agent index in w
+    int* off = nullptr;        // [cap_scenes + 1]
+    int* cursor = nullptr;     // [cap_scenes]
+    int cap_agents = 0, cap_scenes = 0;
+};
+cudaError_t launch_swarm_prep(int n, const int* scene_of_agent, const float* state, int n_scenes, SwarmScratch& s,
+                              cudaStream_t st);
+cudaError_t launch_swarm_proximity(int n, const int* scene_of_agent, const float* state, int n_scenes,
+                                   const SwarmScratch& s, float radius, float* dist, int* other, int* n_collide,
+                                   cudaStream_t st);
 size_t render_smem_bytes(int warps_per_cta, int stack_depth, int rpl);
 int render_config_list(sim_render_config* out, int max);
 bool render_config_valid(const sim_render_config& c);

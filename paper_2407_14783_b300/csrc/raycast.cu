@@ -65,6 +65,33 @@ __device__ __forceinline__ void mt_test(Ray& r, const float4 a, const float4 b, 
     }
 }
 
+// Ray against drone j's box (multi-agent mode): move the ray into the drone's
+// frame (c_k = body axis k with the centre's k-th world coordinate in w) and
+// slab-test the half extents h.  The hit is the entry distance, or the exit
+// distance when the ray starts inside; it competes with the triangles under
+// the same (t, unsigned id) order with id = INT_MIN + j.
+__device__ __forceinline__ void drone_test(Ray& r, const float4 c0, const float4 c1, const float4 c2, const float h[3],
+                                           int code) {
+    const float dx = r.o[0] - c0.w, dy = r.o[1] - c1.w, dz = r.o[2] - c2.w;
+    const float4 c[3] = {c0, c1, c2};
+    float tn = -INFINITY, tf = INFINITY;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float ol = c[k].x * dx + c[k].y * dy + c[k].z * dz;
+        const float dl = c[k].x * r.d[0] + c[k].y * r.d[1] + c[k].z * r.d[2];
+        const float inv = 1.0f / (fabsf(dl) > 1e-20f ? dl : copysignf(1e-20f, dl));
+        const float t0 = (-h[k] - ol) * inv, t1 = (h[k] - ol) * inv;
+        tn = fmaxf(tn, fminf(t0, t1));
+        tf = fminf(tf, fmaxf(t0, t1));
+    }
+    const float t = tn > kTmin ? tn : tf;
+    const bool hit = tn <= tf && t > kTmin && (t < r.best_t || (t == r.best_t && (unsigned)code < (unsigned)r.best_id));
+    if (hit && r.live) {
+        r.best_t = t;
+        r.best_id = code;
+    }
+}
+
 // Slab test of one child box against a ray; entry distance in tn.
 __device__ __forceinline__ bool slab(const Ray& r, float lx, float ly, float lz, float hx, float hy, float hz,
                                      float& tn) {
@@ -146,6 +173,17 @@ __device__ __noinline__ void copy_out(const uint8_t* src, uint8_t* dst, size_t b
         for (size_t i = lane; i < bytes / 16; i += 32) d[i] = __ldcg(s + i);
     } else {
         for (size_t i = lane; i < bytes; i += 32) dst[i] = __ldcg(src + i);
+    }
+}
+
+// Bounds of a tile's ray segments (per-lane bounds reduced over the warp), padded.
+__device__ __forceinline__ void tile_bounds(const float flo[3], const float fhi[3], float blo[3], float bhi[3]) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float lo = warp_min(flo[j]), hi = warp_max(fhi[j]);
+        const float pad = 1e-3f * (hi - lo) + 1e-4f;
+        blo[j] = lo - pad;
+        bhi[j] = hi + pad;
     }
 }
 
@@ -315,16 +353,46 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
 
         int item_cost = 0;
         if (scene_ok) {
+            // other drones of the scene (multi-agent mode): cull their bounding
+            // spheres against the bounds of the tile's ray segments, then test
+            // each survivor's box
+            if (A.drones) {
+                float blo[3], bhi[3];
+                tile_bounds(flo, fhi, blo, bhi);
+                const int m_lo = __ldg(A.swarm_off + sid), m_hi = __ldg(A.swarm_off + sid + 1);
+                const float rad = A.swarm_radius;
+                const float4 none = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(agent));
+                // two groups of 32 members per pass, both loads in flight together
+                for (int k0 = m_lo; k0 < m_hi; k0 += 64) {
+                    float4 sph[2];
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {
+                        const int k = k0 + 32 * g + lane;
+                        sph[g] = k < m_hi ? __ldg(A.swarm_spheres + k) : none;
+                    }
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {
+                        const int j = __float_as_int(sph[g].w);
+                        const bool keep = j != agent && sph[g].x - rad <= bhi[0] && sph[g].x + rad >= blo[0] &&
+                                          sph[g].y - rad <= bhi[1] && sph[g].y + rad >= blo[1] &&
+                                          sph[g].z - rad <= bhi[2] && sph[g].z + rad >= blo[2];
+                        unsigned mask = __ballot_sync(kFull, keep);
+                        while (mask) {
+                            const int src = __ffs(mask) - 1;
+                            mask &= mask - 1;
+                            const int jj = __shfl_sync(kFull, j, src);
+                            const float4 c0 = __ldg(A.drones + 3 * (size_t)jj), c1 = __ldg(A.drones + 3 * (size_t)jj + 1),
+                                         c2 = __ldg(A.drones + 3 * (size_t)jj + 2);
+#pragma unroll
+                            for (int q = 0; q < RPL; ++q) drone_test(ray[q], c0, c1, c2, A.swarm_half, INT_MIN + jj);
+                        }
+                    }
+                }
+            }
             // large triangles: cull against the tile's ray-segment bounds, test the rest
             if (row.n_large > 0) {
                 float blo[3], bhi[3];
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const float lo = warp_min(flo[j]), hi = warp_max(fhi[j]);
-                    const float pad = 1e-3f * (hi - lo) + 1e-4f;
-                    blo[j] = lo - pad;
-                    bhi[j] = hi + pad;
-                }
+                tile_bounds(flo, fhi, blo, bhi);
                 for (int k0 = 0; k0 < row.n_large; k0 += 32) {
                     const int k = k0 + lane;
                     bool keep = false;
@@ -563,9 +631,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                 if (nz.enabled) dv = noisy(dv, A.cam.max_depth, nz.d_gauss, nz.d_speckle, nz.d_shot, nz.d_sp, nz.seed, nb);
                 A.depth[off] = dv;
             }
-            if (in && A.hit_id) A.hit_id[off] = ray[q].best_id;
+            // ids: triangle >= 0, miss -1, drone j (internal INT_MIN + j) -2 - j
+            const int bid = ray[q].best_id;
+            const bool drone = bid < -1;
+            if (in && A.hit_id) A.hit_id[off] = drone ? -2 - (bid - INT_MIN) : bid;
             if (in && A.seg) {
-                int lab = ray[q].best_id >= 0 ? (row.labels ? __ldg(row.labels + ray[q].best_id) : ray[q].best_id) : -1;
+                int lab = bid >= 0 ? (row.labels ? __ldg(row.labels + bid) : bid) : drone ? A.swarm_label : -1;
                 if (nz.enabled && nz.s_models && lab >= 0)
                     lab = (int)rintf(noisy((float)lab, nz.s_max, nz.s_gauss, nz.s_speckle, nz.s_shot, nz.s_sp, nz.seed,
                                            nb + 32));
@@ -574,7 +645,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                 A.seg[off] = lab;
             }
             if (A.rgb) {
-                const uint32_t col = ray[q].best_id >= 0 ? __ldg(row.colors + ray[q].best_id) : 0u;
+                const uint32_t col = bid >= 0 ? __ldg(row.colors + bid) : drone ? A.swarm_rgb : 0u;
                 const int p = lane + 32 * q;
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {

@@ -187,6 +187,30 @@ class Sim:
         B.check(rc, "sim_nearest_obstacle", self.h)
         return dist, point, tri
 
+    def set_swarm(self, half=None, rgb=(255, 255, 255), label: int = -2):
+        """Multi-agent mode: agents sharing a scene see each other's drones, boxes
+        of half extents `half` (m); None returns to the parallel-agents mode."""
+        if half is None:
+            B.check(self.L.sim_set_swarm(self.h, None), "sim_set_swarm", self.h)
+            return
+        cfg = B.SimSwarm((ctypes.c_float * 3)(*[float(x) for x in half]), (ctypes.c_uint8 * 3)(*[int(x) for x in rgb]),
+                         int(label))
+        B.check(self.L.sim_set_swarm(self.h, ctypes.byref(cfg)), "sim_set_swarm", self.h)
+
+    def swarm_proximity(self, scene_of_agent, state, radius: float, stream=None):
+        """Per agent, over the other agents of its scene: (nearest centre distance,
+        that agent, number closer than 2 radius)."""
+        n = state.shape[1]
+        _need(scene_of_agent, torch.int32, (n,), "scene_of_agent")
+        _need(state, torch.float32, (STATE_DIM, n), "state")
+        dist = torch.empty((n,), device=state.device)
+        other = torch.empty((n,), dtype=torch.int32, device=state.device)
+        hits = torch.empty((n,), dtype=torch.int32, device=state.device)
+        rc = self.L.sim_swarm_proximity(self.h, n, _ptr(scene_of_agent), _ptr(state), float(radius), _ptr(dist),
+                                        _ptr(other), _ptr(hits), _stream(stream))
+        B.check(rc, "sim_swarm_proximity", self.h)
+        return dist, other, hits
+
     def render_seg(self, scene_of_agent, state, depth=None, rgb=None, hit=None, seg=None, stream=None):
         """Render with a segmentation image (labels of sim_scene_set_labels, -1 on a miss)."""
         n = state.shape[1]
