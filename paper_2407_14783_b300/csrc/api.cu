@@ -1332,6 +1332,33 @@ namespace vf {
 
 int ctx_alloc_ext(sim_ctx* c, size_t bytes, void** out) { return ctx_alloc(c, bytes, out); }
 void ctx_free_ext(sim_ctx* c, void* p, size_t bytes) { ctx_free(c, p, bytes); }
+
+// Stream-ordered allocation from `pool` on stream s, counted against the
+// context's budget like ctx_alloc.  Unlike cudaFree, returning a block does
+// not synchronise the device: the pool reuses it once s has passed the free.
+int ctx_alloc_pool(sim_ctx* c, size_t bytes, void** out, cudaMemPool_t pool, cudaStream_t s) {
+    *out = nullptr;
+    if (bytes == 0) bytes = 16;
+    std::lock_guard<std::mutex> lk(c->alloc_mu);
+    if (c->budget && c->used + bytes > c->budget)
+        return fail(SIM_ERR_BUDGET, "memory budget exceeded: need " + std::to_string(bytes) + " B, used " +
+                                        std::to_string(c->used) + " of " + std::to_string(c->budget));
+    cudaError_t e = cudaMallocFromPoolAsync(out, bytes, pool, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return cuda_fail(e, "cudaMallocFromPoolAsync");
+    }
+    c->used += bytes;
+    return SIM_OK;
+}
+void ctx_free_pool(sim_ctx* c, void* p, size_t bytes, cudaStream_t s) {
+    if (!p) return;
+    cudaFreeAsync(p, s);
+    if (bytes == 0) bytes = 16;
+    std::lock_guard<std::mutex> lk(c->alloc_mu);
+    c->used -= bytes;
+}
 void ctx_image_size(const sim_ctx* c, int* W, int* H) {
     *W = c->cam.W;
     *H = c->cam.H;

@@ -131,6 +131,8 @@ cudaError_t launch_nearest(const NearestArgs& a, cudaStream_t s);
 // api.cu: context services for the step server.
 int ctx_alloc_ext(sim_ctx* c, size_t bytes, void** out);
 void ctx_free_ext(sim_ctx* c, void* p, size_t bytes);
+int ctx_alloc_pool(sim_ctx* c, size_t bytes, void** out, cudaMemPool_t pool, cudaStream_t s);
+void ctx_free_pool(sim_ctx* c, void* p, size_t bytes, cudaStream_t s);
 void ctx_image_size(const sim_ctx* c, int* W, int* H);
 bool ctx_scene_live(sim_ctx* c, int scene_id);
 int ctx_step(sim_ctx* c, int n, float* state, const float* cmd, cudaStream_t s);

@@ -100,6 +100,9 @@ struct sim_server {
     PackEntry* h_tab[kRing] = {};
     cudaEvent_t it_ev[kRing] = {};
     std::vector<std::pair<void*, size_t>> owned;
+    // per-request input blocks come from this stream-ordered pool: admitting
+    // and retiring requests never synchronises the device
+    cudaMemPool_t pool = nullptr;
 
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -134,7 +137,7 @@ void finish(sim_server* S, Req* r, int code) {
 }
 
 void release_inputs(sim_server* S, Req* r) {
-    if (r->d_in) vf::ctx_free_ext(S->ctx, r->d_in, r->d_bytes);
+    if (r->d_in) vf::ctx_free_pool(S->ctx, r->d_in, r->d_bytes, S->stream);
     r->d_in = nullptr;
     if (r->ev) cudaEventDestroy(r->ev);
     r->ev = nullptr;
@@ -173,7 +176,7 @@ void admit(sim_server* S, int& n_active) {
         const int n = r->spec.n_agents, T = r->spec.n_steps;
         const size_t bytes = sizeof(float) * ((size_t)vf::kStateDim * n + (size_t)T * vf::kCmdDim * n);
         void* p = nullptr;
-        const int rc = vf::ctx_alloc_ext(S->ctx, bytes, &p);
+        const int rc = vf::ctx_alloc_pool(S->ctx, bytes, &p, S->pool, S->stream);
         // memory admission: wait until memory frees up, unless nothing is running
         // that could free it (then the request can never fit the budget)
         if (rc == SIM_ERR_BUDGET && (!S->active.empty() || !S->draining.empty())) return;
@@ -193,7 +196,7 @@ void admit(sim_server* S, int& n_active) {
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            vf::ctx_free_ext(S->ctx, r->d_in, r->d_bytes);
+            vf::ctx_free_pool(S->ctx, r->d_in, r->d_bytes, S->stream);
             r->d_in = nullptr;
             finish(S, r, SIM_ERR_CUDA);
             continue;
@@ -372,7 +375,11 @@ void free_server(sim_server* S) {
         if (S->h_tab[k]) cudaFreeHost(S->h_tab[k]);
         if (S->it_ev[k]) cudaEventDestroy(S->it_ev[k]);
     }
-    if (S->stream) cudaStreamDestroy(S->stream);
+    if (S->stream) {
+        cudaStreamSynchronize(S->stream);
+        cudaStreamDestroy(S->stream);
+    }
+    if (S->pool) cudaMemPoolDestroy(S->pool);
     for (auto& kv : S->all) {
         if (kv.second->ev) cudaEventDestroy(kv.second->ev);
         delete kv.second;
@@ -402,6 +409,21 @@ int sim_server_create(sim_ctx* ctx, sim_server** out, int32_t capacity) {
     int rc = SIM_OK;
     cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) rc = SIM_ERR_CUDA;
+    if (rc == SIM_OK) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = S->device;
+        if (cudaMemPoolCreate(&S->pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            S->pool = nullptr;
+            rc = SIM_ERR_CUDA;
+        } else {
+            // keep freed blocks in the pool for the next requests
+            unsigned long long keep = ~0ull;
+            cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+    }
     for (int k = 0; k < 2 && rc == SIM_OK; ++k)
         if ((rc = alloc_owned(S, sizeof(float) * vf::kStateDim * n, &p)) == SIM_OK) S->d_state[k] = (float*)p;
     if (rc == SIM_OK && (rc = alloc_owned(S, sizeof(float) * vf::kCmdDim * n, &p)) == SIM_OK) S->d_cmd = (float*)p;
