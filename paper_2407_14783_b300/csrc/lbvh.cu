@@ -450,6 +450,261 @@ __global__ void pack_colors_kernel(int n, const uint8_t* __restrict__ rgb, uint3
                 ((uint32_t)rgb[3 * (size_t)i + 2] << 16);
 }
 
+// ------------------------------------------------------------ PLOC
+// The binary radix tree above splits by Morton prefix; its upper levels are
+// then rebuilt by parallel locally-ordered clustering (Meister and Bittner
+// 2018): the leaves of the packed radix tree (ranges of at most kLeafMax
+// triangles, contiguous in Morton order) are the initial clusters, and every
+// round each cluster finds, within kPlocRadius positions of the Morton-ordered
+// list, the neighbour whose union box has the smallest surface area; mutual
+// nearest neighbours merge into a new node and the list is compacted.  The
+// surface-area-guided tree needs fewer node visits per ray than the prefix
+// splits.  Node ids come from an exclusive scan over the merging pairs, so the
+// tree does not depend on thread timing.
+constexpr int kPlocRadius = 16;
+constexpr int kPlocBlock = 256;
+constexpr int kPlocMaxDepth = 56;  // deeper trees keep the radix-tree layout (traversal stacks hold 64)
+
+__device__ __forceinline__ float half_area(float4 lo, float4 hi) {
+    const float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
+    return dx * dy + dy * dz + dz * dx;
+}
+
+// The packed radix tree's leaves: the children with at most kLeafMax
+// triangles of internal nodes with more.  At the leaf's first sorted position:
+// code_at = its leaf code (0 elsewhere: leaf codes are < 0) and src_at = where
+// its box is (>= 0 internal radix node, < 0: -1 - sorted triangle position).
+__global__ void ploc_leaves_kernel(int n, const int2* __restrict__ child, const int2* __restrict__ range,
+                                   int* __restrict__ code_at, int* __restrict__ src_at) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int2 r = range[i];
+    if (r.y - r.x + 1 <= kLeafMax) return;  // inside a leaf of its ancestor
+    const int2 c = child[i];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int cc = s == 0 ? c.x : c.y;
+        if (cc < 0) {
+            const int j = -1 - cc;
+            code_at[j] = leaf_code(j, 1);
+            src_at[j] = cc;
+        } else {
+            const int2 rc = range[cc];
+            const int cnt = rc.y - rc.x + 1;
+            if (cnt > kLeafMax) continue;
+            code_at[rc.x] = leaf_code(rc.x, cnt);
+            src_at[rc.x] = cc;
+        }
+    }
+}
+
+__global__ void ploc_flags_kernel(int n, const int* __restrict__ code_at, uint32_t* __restrict__ flag) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) flag[j] = code_at[j] != 0 ? 1u : 0u;
+    if (j == n) flag[n] = 0u;
+}
+
+// Leaf k of the cluster list (Morton order): pool node k.
+__global__ void ploc_gather_kernel(int n, const uint32_t* __restrict__ off, const int* __restrict__ code_at,
+                                   const int* __restrict__ src_at, const uint32_t* __restrict__ order,
+                                   const float4* __restrict__ tlo, const float4* __restrict__ thi,
+                                   const float4* __restrict__ node_lo, const float4* __restrict__ node_hi,
+                                   int* __restrict__ leaf_code_of, float4* __restrict__ plo, float4* __restrict__ phi,
+                                   int* __restrict__ clusters) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n || code_at[j] == 0) return;
+    const int k = (int)off[j];
+    const int src = src_at[j];
+    leaf_code_of[k] = code_at[j];
+    if (src < 0) {
+        const uint32_t tri = order[-1 - src];
+        plo[k] = tlo[tri];
+        phi[k] = thi[tri];
+    } else {
+        plo[k] = node_lo[src];
+        phi[k] = node_hi[src];
+    }
+    clusters[k] = k;
+}
+
+// Nearest neighbour of every cluster within kPlocRadius positions: smallest
+// union surface area, lowest position among equals.
+__global__ void __launch_bounds__(kPlocBlock) ploc_nn_kernel(int m, const int* __restrict__ clusters,
+                                                             const float4* __restrict__ plo,
+                                                             const float4* __restrict__ phi, int* __restrict__ nn) {
+    __shared__ float4 slo[kPlocBlock + 2 * kPlocRadius], shi[kPlocBlock + 2 * kPlocRadius];
+    const int base = blockIdx.x * kPlocBlock - kPlocRadius;
+    for (int t = threadIdx.x; t < kPlocBlock + 2 * kPlocRadius; t += kPlocBlock) {
+        const int k = base + t;
+        if (k >= 0 && k < m) {
+            const int id = clusters[k];
+            slo[t] = plo[id];
+            shi[t] = phi[id];
+        }
+    }
+    __syncthreads();
+    const int k = blockIdx.x * kPlocBlock + threadIdx.x;
+    if (k >= m) return;
+    const float4 ml = slo[threadIdx.x + kPlocRadius], mh = shi[threadIdx.x + kPlocRadius];
+    float best = INFINITY;
+    int bj = -1;
+    for (int d = -kPlocRadius; d <= kPlocRadius; ++d) {
+        const int j = k + d;
+        if (d == 0 || j < 0 || j >= m) continue;
+        const float4 ol = slo[threadIdx.x + kPlocRadius + d], oh = shi[threadIdx.x + kPlocRadius + d];
+        const float4 ul = make_float4(fminf(ml.x, ol.x), fminf(ml.y, ol.y), fminf(ml.z, ol.z), 0.0f);
+        const float4 uh = make_float4(fmaxf(mh.x, oh.x), fmaxf(mh.y, oh.y), fmaxf(mh.z, oh.z), 0.0f);
+        const float a = half_area(ul, uh);
+        if (a < best) {
+            best = a;
+            bj = j;
+        }
+    }
+    nn[k] = bj;
+}
+
+// keep[k]: cluster k survives the round; make[k]: it merges with its (later)
+// mutual nearest neighbour into a new node.  Entry m of both is 0, so an
+// exclusive scan of m + 1 entries ends with the totals.
+__global__ void ploc_mark_kernel(int m, const int* __restrict__ nn, uint32_t* __restrict__ keep,
+                                 uint32_t* __restrict__ make) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > m) return;
+    if (k == m) {
+        keep[m] = 0u;
+        make[m] = 0u;
+        return;
+    }
+    const int j = nn[k];
+    const bool mutual = j >= 0 && nn[j] == k;
+    keep[k] = (mutual && k > j) ? 0u : 1u;
+    make[k] = (mutual && k < j) ? 1u : 0u;
+}
+
+__global__ void ploc_apply_kernel(int m, int m0, int node_base, const int* __restrict__ clusters,
+                                  const int* __restrict__ nn, const uint32_t* __restrict__ keep_off,
+                                  const uint32_t* __restrict__ make_off, float4* __restrict__ plo,
+                                  float4* __restrict__ phi, int2* __restrict__ pchild, int* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    const int j = nn[k];
+    const bool mutual = j >= 0 && nn[j] == k;
+    if (mutual && k > j) return;  // merged into cluster j's new node
+    int id = clusters[k];
+    if (mutual) {
+        const int b = clusters[j];
+        const int nid = node_base + (int)make_off[k];
+        const float4 al = plo[id], ah = phi[id], bl = plo[b], bh = phi[b];
+        plo[nid] = make_float4(fminf(al.x, bl.x), fminf(al.y, bl.y), fminf(al.z, bl.z), 0.0f);
+        phi[nid] = make_float4(fmaxf(ah.x, bh.x), fmaxf(ah.y, bh.y), fmaxf(ah.z, bh.z), 0.0f);
+        pchild[nid - m0] = make_int2(id, b);
+        id = nid;
+    }
+    out[keep_off[k]] = id;
+}
+
+// Parent of every internal pool node (internal t = pool id m0 + t).
+__global__ void ploc_parent_kernel(int n_int, int m0, const int2* __restrict__ pchild, int* __restrict__ parent) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_int) return;
+    const int2 c = pchild[t];
+    if (c.x >= m0) parent[c.x - m0] = t;
+    if (c.y >= m0) parent[c.y - m0] = t;
+}
+
+// Depth of every internal node (root 0), bounded walk; the tree's depth
+// (internal levels plus the leaf level) goes to max_depth.
+__global__ void ploc_depth_kernel(int n_int, const int* __restrict__ parent, int* __restrict__ depth,
+                                  int* __restrict__ max_depth) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_int) return;
+    int d = 0;
+    for (int p = parent[t]; p >= 0 && d <= kMaxTreeDepth; p = parent[p]) ++d;
+    depth[t] = d;
+    atomicMax(max_depth, d + 1);
+}
+
+__device__ __forceinline__ void pool_child(int id, int m0, const int* __restrict__ leaf_code_of,
+                                           const float4* __restrict__ plo, const float4* __restrict__ phi, float pad,
+                                           float4& lo, float4& hi, int& code) {
+    lo = plo[id];
+    hi = phi[id];
+    lo.x -= pad; lo.y -= pad; lo.z -= pad;
+    hi.x += pad; hi.y += pad; hi.z += pad;
+    code = id < m0 ? leaf_code_of[id] : id - m0;
+}
+
+__global__ void ploc_pack_kernel(int n_int, int m0, const int2* __restrict__ pchild, const int* __restrict__ leaf_code_of,
+                                 const float4* __restrict__ plo, const float4* __restrict__ phi, float pad,
+                                 float4* __restrict__ nodes) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_int) return;
+    const int2 c = pchild[t];
+    float4 l0, h0, l1, h1;
+    int c0, c1;
+    pool_child(c.x, m0, leaf_code_of, plo, phi, pad, l0, h0, c0);
+    pool_child(c.y, m0, leaf_code_of, plo, phi, pad, l1, h1, c1);
+    nodes[4 * (size_t)t + 0] = make_float4(l0.x, l0.y, l0.z, h0.x);
+    nodes[4 * (size_t)t + 1] = make_float4(h0.y, h0.z, l1.x, l1.y);
+    nodes[4 * (size_t)t + 2] = make_float4(l1.z, h1.x, h1.y, h1.z);
+    nodes[4 * (size_t)t + 3] = make_float4(__int_as_float(c0), __int_as_float(c1), 0.0f, 0.0f);
+}
+
+// 4-wide nodes from packed binary nodes (the same layout pack_wide_kernel
+// writes): for every even-depth node t its children, each internal child
+// replaced by that child's two children.  Boxes are already padded.
+__global__ void wide_from_nodes_kernel(int n_int, const float4* __restrict__ nodes, const int* __restrict__ depth,
+                                       float4* __restrict__ wide) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_int || (depth[t] & 1)) return;
+    float bl[4][3], bh[4][3];
+    int code[4];
+    int k = 0;
+    auto slot_of = [&](const float4* np, int s, float* lo, float* hi, int& cd) {
+        const float4 a = np[0], b = np[1], c = np[2], d = np[3];
+        if (s == 0) {
+            lo[0] = a.x; lo[1] = a.y; lo[2] = a.z; hi[0] = a.w; hi[1] = b.x; hi[2] = b.y;
+            cd = __float_as_int(d.x);
+        } else {
+            lo[0] = b.z; lo[1] = b.w; lo[2] = c.x; hi[0] = c.y; hi[1] = c.z; hi[2] = c.w;
+            cd = __float_as_int(d.y);
+        }
+    };
+    const float4* np = nodes + 4 * (size_t)t;
+    for (int s = 0; s < 2; ++s) {
+        float lo[3], hi[3];
+        int cd;
+        slot_of(np, s, lo, hi, cd);
+        if (cd >= 0) {
+            const float4* gp = nodes + 4 * (size_t)cd;
+            for (int u = 0; u < 2; ++u) {
+                slot_of(gp, u, bl[k], bh[k], code[k]);
+                ++k;
+            }
+        } else {
+            for (int j = 0; j < 3; ++j) {
+                bl[k][j] = lo[j];
+                bh[k][j] = hi[j];
+            }
+            code[k++] = cd;
+        }
+    }
+    for (; k < 4; ++k) {
+        for (int j = 0; j < 3; ++j) bl[k][j] = bh[k][j] = 1.0e30f;
+        code[k] = kEmptyRoot;
+    }
+    float4* w = wide + 8 * (size_t)t;
+    w[0] = make_float4(bl[0][0], bl[1][0], bl[2][0], bl[3][0]);
+    w[1] = make_float4(bl[0][1], bl[1][1], bl[2][1], bl[3][1]);
+    w[2] = make_float4(bl[0][2], bl[1][2], bl[2][2], bl[3][2]);
+    w[3] = make_float4(bh[0][0], bh[1][0], bh[2][0], bh[3][0]);
+    w[4] = make_float4(bh[0][1], bh[1][1], bh[2][1], bh[3][1]);
+    w[5] = make_float4(bh[0][2], bh[1][2], bh[2][2], bh[3][2]);
+    w[6] = make_float4(__int_as_float(code[0]), __int_as_float(code[1]), __int_as_float(code[2]),
+                       __int_as_float(code[3]));
+    w[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 __global__ void init_bounds_kernel(int* b) {
     if (threadIdx.x < 3) b[threadIdx.x] = 0x7FFFFFFF;
     else if (threadIdx.x < 6) b[threadIdx.x] = (int)0x80000000;
@@ -464,6 +719,92 @@ inline unsigned nb(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
     } while (0)
 
 }  // namespace
+
+// Scratch of the clustering, mostly buffers of the radix build that are dead
+// by then; the node pool (boxes and children, 72 bytes per leaf cluster)
+// lives in the scene's 4-wide node buffer, which is written last.
+struct PlocScratch {
+    int* code_at;       // [n]   (the large-triangle flags, dead after the Morton codes)
+    int* src_at;        // [n]
+    uint32_t* flag;     // [n + 1]
+    int* leaf_code_of;  // [n]
+    int* c0;            // [n]
+    int* c1;            // [n]   (the spare sort values buffer)
+    int* nn;            // [n]   (later the depth of every internal node)
+    uint32_t* keep;     // [n]   (the sorted keys, dead after the hierarchy)
+    uint32_t* make;     // [n]   (the spare sort keys buffer)
+};
+
+// Rebuild the tree above the radix tree's leaves by PLOC and pack it into
+// out->nodes / out->wide.  *ok = false when it gives up (no progress in a
+// round, or a tree deeper than kPlocMaxDepth): the caller then packs the radix
+// tree, which overwrites everything this wrote.
+cudaError_t ploc_build(int n_bvh, const uint32_t* order, const float4* tlo, const float4* thi, const int2* child,
+                       const int2* range, const float4* node_lo, const float4* node_hi, const PlocScratch& w,
+                       int* misc, float pad, LbvhResult* out, bool* ok, cudaStream_t s) {
+    *ok = false;
+    VF_TRY(cudaMemsetAsync(w.code_at, 0, sizeof(int) * (size_t)n_bvh, s));
+    ploc_leaves_kernel<<<nb(n_bvh - 1, 256), 256, 0, s>>>(n_bvh, child, range, w.code_at, w.src_at);
+    ploc_flags_kernel<<<nb(n_bvh + 1, 256), 256, 0, s>>>(n_bvh, w.code_at, w.flag);
+    scan_kernel<<<1, 1024, 0, s>>>(w.flag, n_bvh + 1);
+    VF_TRY(cudaGetLastError());
+    uint32_t m0u;
+    VF_TRY(cudaMemcpyAsync(&m0u, w.flag + n_bvh, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    VF_TRY(cudaStreamSynchronize(s));
+    const int m0 = (int)m0u;
+    // a radix tree over n_bvh >= 2 triangles has a leaf of two or more, so m0 < n_bvh
+    if (m0 < 2 || m0 >= n_bvh) return cudaSuccess;
+    // node pool in the 4-wide buffer (128 (n_bvh - 1) bytes >= 72 m0)
+    float4* plo = out->wide;
+    float4* phi = plo + 2 * (size_t)m0;
+    int2* pchild = reinterpret_cast<int2*>(phi + 2 * (size_t)m0);
+    ploc_gather_kernel<<<nb(n_bvh, 256), 256, 0, s>>>(n_bvh, w.flag, w.code_at, w.src_at, order, tlo, thi, node_lo,
+                                                      node_hi, w.leaf_code_of, plo, phi, w.c0);
+    int* cur = w.c0;
+    int* nxt = w.c1;
+    int m = m0, created = 0;
+    for (int round = 0; m > 1; ++round) {
+        if (round > 4096) return cudaSuccess;
+        ploc_nn_kernel<<<nb(m, kPlocBlock), kPlocBlock, 0, s>>>(m, cur, plo, phi, w.nn);
+        ploc_mark_kernel<<<nb(m + 1, 256), 256, 0, s>>>(m, w.nn, w.keep, w.make);
+        scan_kernel<<<1, 1024, 0, s>>>(w.keep, m + 1);
+        scan_kernel<<<1, 1024, 0, s>>>(w.make, m + 1);
+        ploc_apply_kernel<<<nb(m, 256), 256, 0, s>>>(m, m0, m0 + created, cur, w.nn, w.keep, w.make, plo, phi, pchild,
+                                                     nxt);
+        VF_TRY(cudaGetLastError());
+        uint32_t kept, made;
+        VF_TRY(cudaMemcpyAsync(&kept, w.keep + m, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        VF_TRY(cudaMemcpyAsync(&made, w.make + m, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        VF_TRY(cudaStreamSynchronize(s));
+        if ((int)kept >= m || created + (int)made > m0 - 1) return cudaSuccess;
+        created += (int)made;
+        m = (int)kept;
+        std::swap(cur, nxt);
+    }
+    const int n_int = m0 - 1;
+    if (created != n_int) return cudaSuccess;
+    int root;
+    VF_TRY(cudaMemcpyAsync(&root, cur, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int* parent = nxt;    // the cluster lists are done with
+    int* depth = w.nn;
+    VF_TRY(cudaMemsetAsync(parent, 0xFF, sizeof(int) * (size_t)n_int, s));  // -1: the root
+    VF_TRY(cudaMemsetAsync(misc + 14, 0, sizeof(int), s));
+    ploc_parent_kernel<<<nb(n_int, 256), 256, 0, s>>>(n_int, m0, pchild, parent);
+    ploc_depth_kernel<<<nb(n_int, 256), 256, 0, s>>>(n_int, parent, depth, misc + 14);
+    VF_TRY(cudaGetLastError());
+    int tree_depth;
+    VF_TRY(cudaMemcpyAsync(&tree_depth, misc + 14, sizeof(int), cudaMemcpyDeviceToHost, s));
+    VF_TRY(cudaStreamSynchronize(s));
+    if (tree_depth > kPlocMaxDepth || root != m0 + n_int - 1) return cudaSuccess;
+    ploc_pack_kernel<<<nb(n_int, 256), 256, 0, s>>>(n_int, m0, pchild, w.leaf_code_of, plo, phi, pad, out->nodes);
+    // the pool is read for the last time above: the 4-wide nodes overwrite it
+    wide_from_nodes_kernel<<<nb(n_int, 256), 256, 0, s>>>(n_int, out->nodes, depth, out->wide);
+    VF_TRY(cudaGetLastError());
+    out->root = root - m0;
+    out->depth = tree_depth;
+    *ok = true;
+    return cudaSuccess;
+}
 
 // Build on `s`; device inputs verts [nv][3], tris [nt][3] (validated), rgb [nt][3].
 // Scratch comes from `scratch` (size lbvh_scratch_bytes(nt)).  Outputs are
@@ -495,7 +836,14 @@ cudaError_t lbvh_build(int64_t nt, const float* d_verts, const int* d_tris, cons
     float4* node_lo = (float4*)take(sizeof(float4) * n);
     float4* node_hi = (float4*)take(sizeof(float4) * n);
     int* flags = (int*)take(sizeof(int) * n);
-    int* misc = (int*)take(sizeof(int) * 16);  // [0..5] bounds, [6..11] centroid bounds, 12 n_large, 13 depth
+    int* misc = (int*)take(sizeof(int) * 16);  // [0..5] bounds, [6..11] centroid bounds, 12 n_large, 13 depth,
+                                               // 14 clustered-tree depth
+    PlocScratch pw;
+    pw.src_at = (int*)take(sizeof(int) * n);
+    pw.flag = (uint32_t*)take(sizeof(uint32_t) * ((size_t)n + 1));
+    pw.leaf_code_of = (int*)take(sizeof(int) * n);
+    pw.c0 = (int*)take(sizeof(int) * n);
+    pw.nn = (int*)take(sizeof(int) * n);
 
     init_bounds_kernel<<<1, 32, 0, s>>>(misc);
     init_bounds_kernel<<<1, 32, 0, s>>>(misc + 6);
@@ -538,18 +886,29 @@ cudaError_t lbvh_build(int64_t nt, const float* d_verts, const int* d_tris, cons
         refit_kernel<<<nb(n_bvh, 256), 256, 0, s>>>(n_bvh, va, tlo, thi, child, parent_int, parent_leaf, node_lo,
                                                     node_hi, flags, misc + 13);
         const float pad = 2.0e-5f * fmaxf(ext, 1e-3f);
-        pack_nodes_kernel<<<nb(n_bvh - 1, 256), 256, 0, s>>>(n_bvh, va, tlo, thi, child, range, node_lo, node_hi,
-                                                             pad, out->nodes);
-        depth_parity_kernel<<<nb(n_bvh - 1, 256), 256, 0, s>>>(n_bvh, parent_int, flags);
-        pack_wide_kernel<<<nb(n_bvh - 1, 256), 256, 0, s>>>(n_bvh, va, tlo, thi, child, range, node_lo, node_hi,
-                                                            flags, pad, out->wide);
         VF_TRY(cudaGetLastError());
         int2 rr;
         VF_TRY(cudaMemcpyAsync(&rr, range, sizeof(int2), cudaMemcpyDeviceToHost, s));
-        VF_TRY(cudaMemcpyAsync(&out->depth, misc + 13, sizeof(int), cudaMemcpyDeviceToHost, s));
         VF_TRY(cudaStreamSynchronize(s));
         const int cnt = rr.y - rr.x + 1;
-        out->root = cnt <= kLeafMax ? leaf_code(0, cnt) : 0;
+        bool clustered = false;
+        pw.code_at = is_large;  // dead buffers of the radix build
+        pw.c1 = (int*)vb;
+        pw.keep = ka;
+        pw.make = kb;
+        if (cnt > kLeafMax)
+            VF_TRY(ploc_build(n_bvh, va, tlo, thi, child, range, node_lo, node_hi, pw, misc, pad, out, &clustered, s));
+        if (!clustered) {
+            pack_nodes_kernel<<<nb(n_bvh - 1, 256), 256, 0, s>>>(n_bvh, va, tlo, thi, child, range, node_lo, node_hi,
+                                                                 pad, out->nodes);
+            depth_parity_kernel<<<nb(n_bvh - 1, 256), 256, 0, s>>>(n_bvh, parent_int, flags);
+            pack_wide_kernel<<<nb(n_bvh - 1, 256), 256, 0, s>>>(n_bvh, va, tlo, thi, child, range, node_lo, node_hi,
+                                                                flags, pad, out->wide);
+            VF_TRY(cudaGetLastError());
+            VF_TRY(cudaMemcpyAsync(&out->depth, misc + 13, sizeof(int), cudaMemcpyDeviceToHost, s));
+            VF_TRY(cudaStreamSynchronize(s));
+            out->root = cnt <= kLeafMax ? leaf_code(0, cnt) : 0;
+        }
     } else if (n_bvh == 1) {
         out->root = leaf_code(0, 1);
         out->depth = 0;
@@ -570,7 +929,9 @@ size_t lbvh_scratch_bytes(int64_t nt) {
     const size_t nblocks = (n + kSortTile - 1) / kSortTile;
     auto r = [](size_t b) { return (b + 255) & ~(size_t)255; };
     return 2 * r(16 * n) + 5 * r(4 * n) + r(4 * 256 * nblocks) + 2 * r(8 * n) + 2 * r(4 * n) + 2 * r(16 * n) +
-           r(4 * n) + r(64);
+           r(4 * n) + r(64) +
+           // clustering: src_at, flag, leaf_code_of, c0, nn
+           r(4 * n) + r(4 * (n + 1)) + 3 * r(4 * n);
 }
 
 }  // namespace vf
