@@ -7,7 +7,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <thread>
 #include <vector>
@@ -510,13 +512,29 @@ cudaError_t launch_cfg(const void* kernel, const RenderArgs& a, int warps_per_ct
     int dev;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (ctas <= 0) {
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * warps_per_cta, smem);
-        if (e != cudaSuccess) return e;
-        ctas = std::max(1, per_sm) * sms;
+        // resident CTAs of a (kernel, block, shared memory) on this device:
+        // queried once, then looked up (the query costs microseconds per launch)
+        static std::mutex mu;
+        static std::map<std::tuple<const void*, int, size_t, int>, int> resident;
+        const auto key = std::make_tuple(kernel, warps_per_cta, smem, dev);
+        int grid = 0;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            const auto it = resident.find(key);
+            if (it != resident.end()) grid = it->second;
+        }
+        if (grid == 0) {
+            int sms = 0, per_sm = 0;
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * warps_per_cta, smem);
+            if (e != cudaSuccess) return e;
+            grid = std::max(1, per_sm) * sms;
+            std::lock_guard<std::mutex> lk(mu);
+            resident[key] = grid;
+        }
+        ctas = grid;
     }
     // never more CTAs than work items need
     const int tiles = ((a.cam.W + 3) / 4) * ((a.cam.H + 1) / 2);  // upper bound over tile shapes

@@ -284,14 +284,23 @@ class Sim:
     # ------------------------------------------------------------ env step with host buffers
     def env_step(self, scene_of_agent, state, cmd_host, depth_host=None, rgb_host=None, state_host=None,
                  stream=None):
+        """One environment step with host buffers (see sim_env_step): host
+        commands in, host images (and optionally the state) out.  Called once
+        per control step, so the marshalling stays minimal: raw pointers, no
+        per-call ctypes objects."""
         n = state.shape[1]
-        for t, name in ((cmd_host, "cmd_host"), (depth_host, "depth_host"), (rgb_host, "rgb_host"),
-                        (state_host, "state_host")):
-            if t is not None and (t.is_cuda or not t.is_contiguous()):
-                raise ValueError(f"{name}: need a contiguous host tensor")
-        rc = self.L.sim_env_step(self.h, n, _ptr(scene_of_agent), _ptr(state), _ptr(cmd_host), _ptr(depth_host),
-                                 _ptr(rgb_host), _ptr(state_host), _stream(stream))
-        B.check(rc, "sim_env_step", self.h)
+        ptr = [None, None, None, None]
+        for i, t in enumerate((cmd_host, depth_host, rgb_host, state_host)):
+            if t is not None:
+                if t.is_cuda or not t.is_contiguous():
+                    raise ValueError(f"{('cmd_host', 'depth_host', 'rgb_host', 'state_host')[i]}: "
+                                     "need a contiguous host tensor")
+                ptr[i] = t.data_ptr()
+        s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        rc = self.L.sim_env_step(self.h, n, scene_of_agent.data_ptr(), state.data_ptr(), ptr[0], ptr[1], ptr[2],
+                                 ptr[3], s)
+        if rc:
+            B.check(rc, "sim_env_step", self.h)
 
     # ------------------------------------------------------------ status
     def status(self, timeout_ms: int = 10000, stream=None) -> int:
