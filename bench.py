@@ -172,9 +172,24 @@ def cpu_baseline_leg(p, scene, w_h, u_h, budget_s=15.0):
         osc.render(p, s)
         t_used += time.perf_counter() - t0
         n += 1
+    # the tiny configuration in full (4 agents, 10 steps, 492 triangles), by
+    # brute force and by the oracle's own BVH
+    tiny = wl.room_scene()
+    st0 = wl.spawn_states(tiny, 4, 11, w_h)
+    tc = wl.uniform_commands(10, 4, 12)
+    tiny_s = {}
+    for mode, bvh in (("brute_force", False), ("bvh", True)):
+        ot = oracle.Scene.from_workload(tiny, bvh=bvh)
+        st = st0.copy()
+        t0 = time.perf_counter()
+        for k in range(10):
+            st = oracle.step(p, st, tc[k])
+            ot.render(p, st, use_bvh=bvh)
+        tiny_s[mode] = 40 / (time.perf_counter() - t0)
     return {"value": sample * n / t_used, "unit": "agent-frames/s", "cores": oracle.num_threads(),
             "kind": "oracle",
-            "sample": f"{n} steps x {sample} agents of the 208,812-triangle room (dynamics + render, FP64)"}
+            "sample": f"{n} steps x {sample} agents of the 208,812-triangle room (dynamics + render, FP64)",
+            "tiny_config_agent_frames_per_s": tiny_s}
 
 
 def _recorded_traffic():
@@ -212,8 +227,11 @@ def raycast_roofline(sim, cnt, n, p, render_ms):
     achieved = alg_bytes / (render_ms * 1e-3) / 1e9
     l2 = sim.probe_read_bandwidth(64 << 20, iters=20)
     hbm, hbm_kind = _peaks()
+    traffic = _recorded_traffic()
+    hbm_achieved = traffic / (render_ms * 1e-3) / 1e9 if traffic else None
     return {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
-            "traffic": _recorded_traffic(), "kernel": "raycast_kernel",
+            "traffic": traffic, "kernel": "raycast_kernel",
+            "hbm_achieved": hbm_achieved, "hbm_frac": hbm_achieved / hbm if hbm_achieved else None,
             "peak_kind": "L2 read bandwidth measured in this run (sim_probe_read_bandwidth, 64 MiB resident)",
             "hbm_peak": hbm, "hbm_peak_kind": hbm_kind, "alg_bytes_per_launch": alg_bytes,
             "launch_ms": render_ms,
@@ -526,8 +544,10 @@ def run_diff(args):
     import oracle
     oracle.build()
     pick = np.array([3, 517])
+    tg = time.perf_counter()
     Lr, gsr, gur = oracle.rollout_loss_grad(p, s0[pick].astype(np.float64), U[:, pick].astype(np.float64),
                                             goals[pick].astype(np.float64), lam)
+    oracle_grad_s = (time.perf_counter() - tg) / len(pick)
     g0n = g0.cpu().numpy().T
     gcn = gc.cpu().numpy().transpose(0, 2, 1)
     errs = []
@@ -542,7 +562,8 @@ def run_diff(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded spawns, goals, commands)",
             "config": {"workload": "differentiable rollout: 1,024 agents, T=200, dt=0.02, checkpoint every 10 steps",
                        "forward_ms": statistics.mean(fw), "backward_ms": statistics.mean(bw),
-                       "grad_rel_err_vs_fp64_oracle": errs, "l2": "state 1024 x 17 floats, L2-resident"},
+                       "grad_rel_err_vs_fp64_oracle": errs, "l2": "state 1024 x 17 floats, L2-resident",
+                       "oracle_grad_s_per_agent": oracle_grad_s},
             "gpu_launches": 2}
     print(json.dumps(line), flush=True)
     sim.close()
