@@ -603,13 +603,57 @@ __global__ void ploc_apply_kernel(int m, int m0, int node_base, const int* __res
     out[keep_off[k]] = id;
 }
 
-// Parent of every internal pool node (internal t = pool id m0 + t).
-__global__ void ploc_parent_kernel(int n_int, int m0, const int2* __restrict__ pchild, int* __restrict__ parent) {
+// Parent of every internal pool node (internal t = pool id m0 + t) and of
+// every leaf cluster.
+__global__ void ploc_parent_kernel(int n_int, int m0, const int2* __restrict__ pchild, int* __restrict__ parent,
+                                   int* __restrict__ parent_leaf) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_int) return;
     const int2 c = pchild[t];
     if (c.x >= m0) parent[c.x - m0] = t;
+    else parent_leaf[c.x] = t;
     if (c.y >= m0) parent[c.y - m0] = t;
+    else parent_leaf[c.y] = t;
+}
+
+// Internal nodes in each subtree, bottom-up from the leaf clusters: at every
+// node the first arriving walk stops, the second sums the children (bounded
+// like the refit).
+__global__ void ploc_size_kernel(int m0, int n_int, const int2* __restrict__ pchild, const int* __restrict__ parent,
+                                 const int* __restrict__ parent_leaf, int* flags, int* size) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m0) return;
+    int p = parent_leaf[k];
+    for (int level = 0; p >= 0 && level <= kMaxTreeDepth; ++level) {
+        __threadfence();
+        if (atomicAdd(&flags[p], 1) == 0) return;
+        __threadfence();
+        const int2 c = pchild[p];
+        const int a = c.x >= m0 ? __ldcg(&size[c.x - m0]) : 0, b = c.y >= m0 ? __ldcg(&size[c.y - m0]) : 0;
+        __stcg(&size[p], 1 + a + b);
+        p = parent[p];
+    }
+}
+
+// Depth-first preorder index of every internal node (root 0, left subtree
+// next): walking up, each step from a right child adds the left sibling's
+// subtree.  In this layout a node's left child follows it in memory.
+__global__ void ploc_dfs_kernel(int n_int, int m0, const int2* __restrict__ pchild, const int* __restrict__ parent,
+                                const int* __restrict__ size, const int* __restrict__ depth, int* __restrict__ index,
+                                int* __restrict__ depth_at) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_int) return;
+    int idx = 0, c = t;
+    for (int level = 0; level <= kMaxTreeDepth; ++level) {
+        const int p = parent[c];
+        if (p < 0) break;
+        const int2 pc = pchild[p];
+        idx += 1;
+        if (pc.y == m0 + c && pc.x >= m0) idx += size[pc.x - m0];
+        c = p;
+    }
+    index[t] = idx;
+    depth_at[idx] = depth[t];
 }
 
 // Depth of every internal node (root 0), bounded walk; the tree's depth
@@ -636,14 +680,17 @@ __device__ __forceinline__ void pool_child(int id, int m0, const int* __restrict
 
 __global__ void ploc_pack_kernel(int n_int, int m0, const int2* __restrict__ pchild, const int* __restrict__ leaf_code_of,
                                  const float4* __restrict__ plo, const float4* __restrict__ phi, float pad,
-                                 float4* __restrict__ nodes) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_int) return;
-    const int2 c = pchild[t];
+                                 const int* __restrict__ index, float4* __restrict__ nodes) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n_int) return;
+    const int2 c = pchild[u];
     float4 l0, h0, l1, h1;
     int c0, c1;
     pool_child(c.x, m0, leaf_code_of, plo, phi, pad, l0, h0, c0);
     pool_child(c.y, m0, leaf_code_of, plo, phi, pad, l1, h1, c1);
+    if (c0 >= 0) c0 = index[c0];
+    if (c1 >= 0) c1 = index[c1];
+    const int t = index[u];
     nodes[4 * (size_t)t + 0] = make_float4(l0.x, l0.y, l0.z, h0.x);
     nodes[4 * (size_t)t + 1] = make_float4(h0.y, h0.z, l1.x, l1.y);
     nodes[4 * (size_t)t + 2] = make_float4(l1.z, h1.x, h1.y, h1.z);
@@ -785,22 +832,32 @@ cudaError_t ploc_build(int n_bvh, const uint32_t* order, const float4* tlo, cons
     if (created != n_int) return cudaSuccess;
     int root;
     VF_TRY(cudaMemcpyAsync(&root, cur, sizeof(int), cudaMemcpyDeviceToHost, s));
-    int* parent = nxt;    // the cluster lists are done with
+    // buffers of the clustering rounds that are done with
+    int* parent = nxt;
     int* depth = w.nn;
+    int* parent_leaf = w.src_at;
+    int* arrivals = reinterpret_cast<int*>(w.make);
+    int* size = reinterpret_cast<int*>(w.keep);
+    int* index = reinterpret_cast<int*>(w.flag);
+    int* depth_at = w.code_at;
     VF_TRY(cudaMemsetAsync(parent, 0xFF, sizeof(int) * (size_t)n_int, s));  // -1: the root
+    VF_TRY(cudaMemsetAsync(arrivals, 0, sizeof(int) * (size_t)n_int, s));
     VF_TRY(cudaMemsetAsync(misc + 14, 0, sizeof(int), s));
-    ploc_parent_kernel<<<nb(n_int, 256), 256, 0, s>>>(n_int, m0, pchild, parent);
+    ploc_parent_kernel<<<nb(n_int, 256), 256, 0, s>>>(n_int, m0, pchild, parent, parent_leaf);
     ploc_depth_kernel<<<nb(n_int, 256), 256, 0, s>>>(n_int, parent, depth, misc + 14);
     VF_TRY(cudaGetLastError());
     int tree_depth;
     VF_TRY(cudaMemcpyAsync(&tree_depth, misc + 14, sizeof(int), cudaMemcpyDeviceToHost, s));
     VF_TRY(cudaStreamSynchronize(s));
     if (tree_depth > kPlocMaxDepth || root != m0 + n_int - 1) return cudaSuccess;
-    ploc_pack_kernel<<<nb(n_int, 256), 256, 0, s>>>(n_int, m0, pchild, w.leaf_code_of, plo, phi, pad, out->nodes);
+    ploc_size_kernel<<<nb(m0, 256), 256, 0, s>>>(m0, n_int, pchild, parent, parent_leaf, arrivals, size);
+    ploc_dfs_kernel<<<nb(n_int, 256), 256, 0, s>>>(n_int, m0, pchild, parent, size, depth, index, depth_at);
+    ploc_pack_kernel<<<nb(n_int, 256), 256, 0, s>>>(n_int, m0, pchild, w.leaf_code_of, plo, phi, pad, index,
+                                                    out->nodes);
     // the pool is read for the last time above: the 4-wide nodes overwrite it
-    wide_from_nodes_kernel<<<nb(n_int, 256), 256, 0, s>>>(n_int, out->nodes, depth, out->wide);
+    wide_from_nodes_kernel<<<nb(n_int, 256), 256, 0, s>>>(n_int, out->nodes, depth_at, out->wide);
     VF_TRY(cudaGetLastError());
-    out->root = root - m0;
+    out->root = 0;  // depth-first order
     out->depth = tree_depth;
     *ok = true;
     return cudaSuccess;
