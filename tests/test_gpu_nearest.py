@@ -54,3 +54,24 @@ def test_nearest_multi_scene_and_walls_only(make_sim, oracle_mod, wl):
         s = wl.spawn_states(sc, k, 40 + sid, 1100.0).astype(np.float32)
         ids = torch.full((k,), sid, dtype=torch.int32, device="cuda")
         _check(sim, oracle_mod.Scene.from_workload(sc, bvh=False), ids, s, 50.0)
+
+
+def test_nearest_zero_agents_and_far_outside(make_sim, oracle_mod, wl):
+    """No agents is a no-op; agents far outside the scene's bounds still get
+    the exact nearest point (the walk prunes nothing wrongly), or max_dist."""
+    p = wl.params()
+    sc = wl.room_scene()
+    sim = make_sim(p)
+    sid = sim.add_workload_scene(sc)
+    from paper_2407_14783_b300.sim import to_soa
+    out = sim.nearest_obstacle(torch.zeros((0,), dtype=torch.int32, device="cuda"),
+                               to_soa(np.zeros((0, 17), np.float32)), 5.0)
+    assert out[0].numel() == 0
+    s = wl.spawn_states(sc, 6, 41, 1100.0).astype(np.float32)
+    s[:, 0:3] += np.array([[40.0, 0, 0], [-35.0, 5, 0], [0, 60.0, 0], [0, 0, 25.0], [0, 0, -30.0], [70.0, 70.0, 70.0]],
+                          np.float32)
+    ids = torch.full((6,), sid, dtype=torch.int32, device="cuda")
+    osc = oracle_mod.Scene.from_workload(sc, bvh=False)
+    d = _check(sim, osc, ids, s, 500.0)
+    assert d.min() > 10.0
+    _check(sim, osc, ids, s, 20.0)

@@ -163,3 +163,17 @@ def test_scheduling_hints_do_not_change_images(make_sim, wl):
             assert np.array_equal(x, y)
     for x, y in zip(small, fresh_small):
         assert np.array_equal(x, y)
+
+
+def test_render_maximum_image_size(make_sim, oracle_mod, wl):
+    """The largest image the library accepts (1024 x 1024) on the large scene:
+    two agents, every pixel against the oracle."""
+    p = wl.params(width=1024, height=1024)
+    sc = wl.cluttered_scene()
+    sim = make_sim(p)
+    sid = sim.add_workload_scene(sc)
+    s = wl.spawn_states(sc, 2, 17, 1100.0).astype(np.float32)
+    d, c, h = _render(sim, sid, s)
+    compare_images(oracle_mod.Scene.from_workload(sc), p, s.astype(np.float64), d, c, h, max_tie_frac=0.02)
+    with pytest.raises(Exception):
+        make_sim(wl.params(width=1025, height=64))

@@ -213,3 +213,19 @@ def test_swarm_proximity_matches_oracle(make_sim, oracle_mod, wl):
         edge = np.any(np.abs(d_all - 2 * radius) < 1e-5, axis=1)
         assert np.array_equal(hits[m][~edge], rh[~edge])
         assert hits[m].sum() > 0
+
+
+def test_single_agent_swarm_equals_parallel_mode(make_sim, wl):
+    """A camera never sees its own drone: one agent per scene renders the same
+    in both modes."""
+    p = wl.params()
+    sa, sb = wl.room_scene(seed=1), wl.room_scene(seed=5)
+    sim = make_sim(p)
+    ida, idb = sim.add_workload_scene(sa), sim.add_workload_scene(sb)
+    st = np.concatenate([_cluster(wl, sa, 1, 50), _cluster(wl, sb, 1, 51)])
+    ids = torch.tensor([ida, idb], dtype=torch.int32, device="cuda")
+    plain = _gpu_render(sim, ids, st)
+    sim.set_swarm(HALF, RGB, LABEL)
+    swarm = _gpu_render(sim, ids, st)
+    for a, b in zip(plain, swarm):
+        assert np.array_equal(a, b)
