@@ -218,6 +218,25 @@ int derive(const sim_params& p, DynConsts& d, CamConsts& cam) {
     d.f_hi = (float)thrust(p.omega_max);
     d.df_lo = thrust(p.omega_min);
     d.df_hi = thrust(p.omega_max);
+    // double-float pairs of the controller constants (hi + lo == the double to ~48 bits)
+    auto pair = [](double v) {
+        const float hi = (float)v;
+        return make_float2(hi, (float)(v - (double)hi));
+    };
+    for (int j = 0; j < 3; ++j) {
+        d.xJ[j] = pair(d.dJ[j]);
+        d.xJK[j] = pair(d.dJK[j]);
+        d.xrate_max[j] = pair(d.drate_max[j]);
+    }
+    for (int r = 0; r < 4; ++r)
+        for (int k = 0; k < 4; ++k) d.xAinv[r][k] = pair(d.dAinv[r][k]);
+    d.xhalf_a_max_m = pair(d.dhalf_a_max_m);
+    d.xf_lo = pair(d.df_lo);
+    d.xf_hi = pair(d.df_hi);
+    d.xk0 = pair(d.dk[0]);
+    d.xk1sq = pair(d.dk[1] * d.dk[1]);
+    d.x4k2 = pair(4.0 * d.dk[2]);
+    d.xhalf_f_hi = pair(0.5 * d.df_hi);
     d.omega_min = p.omega_min;
     d.omega_max = p.omega_max;
     const double h = (double)p.dt / p.n_sub;

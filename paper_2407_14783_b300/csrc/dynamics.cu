@@ -50,32 +50,86 @@ struct CtrlTape {
 // Thrust allocation shared by the controllers, in FP64: rotor thrusts
 // f = Ainv (collective thrust, moment), clamped to the reachable range, and
 // the desired rotor speeds from the thrust polynomial's positive root.
-__device__ __forceinline__ void allocate(const DynConsts& c, const double rhs[4], float omega_des[4],
-                                         CtrlTape* tape) {
+// ---------------------------------------------------------------- double-float
+// A value as the unevaluated sum hi + lo of two floats (about 48 significant
+// bits), built from exact products (FMA) and exact sums (Knuth's two-sum).
+// This GPU runs FP64 at a small fraction of its FP32 rate, so the controller's
+// cancellation-prone steps use these pairs on the FP32 pipes instead.
+struct dfl {
+    float hi, lo;
+};
+// The additions and products below are written with the _rn intrinsics: the
+// compiler never fuses those into FMAs, which would break the exact
+// transformations.
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ dfl df_norm(float hi, float lo) {  // |hi| >= |lo|
+    const float s = __fadd_rn(hi, lo);
+    return {s, __fsub_rn(lo, __fsub_rn(s, hi))};
+}
+__device__ __forceinline__ dfl df_of(float2 c) { return {c.x, c.y}; }
+__device__ __forceinline__ dfl df_of(float a) { return {a, 0.0f}; }
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+    const dfl s = df_two_sum(a.hi, b.hi), t = df_two_sum(a.lo, b.lo);
+    const dfl u = df_norm(s.hi, __fadd_rn(s.lo, t.hi));
+    return df_norm(u.hi, __fadd_rn(u.lo, t.lo));
+}
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = __fmaf_rn(a.hi, b.hi, -p);
+    return df_norm(p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e)));
+}
+__device__ __forceinline__ bool df_lt(dfl a, dfl b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ float df_float(dfl a) { return __fadd_rn(a.hi, a.lo); }
+
+// Rotor speed of thrust fc, the positive root of k2 w^2 + k1 w + k0 = fc
+// (Eq. 4 inverted); dw = dw/dfc.  The discriminant k1^2 - 4 k2 (k0 - fc) is a
+// small difference of larger terms near zero thrust and is formed in double
+// precision; the root is then taken in FP32 in the cancellation-free form
+// w = 2 (fc - k0) / (sqrt(disc) + k1), which equals (sqrt(disc) - k1) / (2 k2).
+__device__ __forceinline__ float rotor_speed(const DynConsts& c, dfl fc, float& dw) {
+    const dfl f0 = df_sub(fc, df_of(c.xk0));
+    if (c.k2 != 0.0f) {
+        const dfl disc = df_add(df_of(c.xk1sq), df_mul(df_of(c.x4k2), f0));
+        const float sq = sqrtf(fmaxf(df_float(disc), 0.0f));
+        const float den = sq + c.k1;
+        dw = sq > 0.0f ? 1.0f / sq : 0.0f;
+        return den > 0.0f ? 2.0f * df_float(f0) / den : 0.0f;
+    }
+    dw = 1.0f / c.k1;
+    return df_float(f0) / c.k1;
+}
+
+// Clamp rotor thrust i to the reachable range, invert it to a rotor speed and
+// clamp that; record what the adjoint needs.
+__device__ __forceinline__ void rotor_command(const DynConsts& c, int i, dfl f, float omega_des[4], CtrlTape* tape) {
+    const dfl lo = df_of(c.xf_lo), hi = df_of(c.xf_hi);
+    const bool in_f = !df_lt(f, lo) && !df_lt(hi, f);
+    const dfl fc = df_lt(f, lo) ? lo : (df_lt(hi, f) ? hi : f);
+    float dw;
+    const float w = rotor_speed(c, fc, dw);
+    const bool in_w = w >= c.omega_min && w <= c.omega_max;
+    omega_des[i] = fminf(fmaxf(w, c.omega_min), c.omega_max);
+    if (tape) {
+        tape->fc[i] = df_float(fc);
+        tape->dw_df[i] = dw;
+        tape->in_f[i] = in_f;
+        tape->in_w[i] = in_w;
+    }
+}
+
+// Mixer: rotor thrusts from (collective thrust, moment), f = A^-1 rhs.
+__device__ __forceinline__ void allocate(const DynConsts& c, const dfl rhs[4], float omega_des[4], CtrlTape* tape) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const double f = c.dAinv[i][0] * rhs[0] + c.dAinv[i][1] * rhs[1] + c.dAinv[i][2] * rhs[2] +
-                         c.dAinv[i][3] * rhs[3];
-        const bool in_f = f >= c.df_lo && f <= c.df_hi;
-        const double fc = fmin(fmax(f, c.df_lo), c.df_hi);
-        double w, dw;
-        if (c.dk[2] != 0.0) {
-            const double disc = c.dk[1] * c.dk[1] - 4.0 * c.dk[2] * (c.dk[0] - fc);
-            const double sq = sqrt(fmax(disc, 0.0));
-            w = (sq - c.dk[1]) / (2.0 * c.dk[2]);
-            dw = disc > 0.0 ? 1.0 / sq : 0.0;
-        } else {
-            w = (fc - c.dk[0]) / c.dk[1];
-            dw = 1.0 / c.dk[1];
-        }
-        const bool in_w = w >= c.domega_min && w <= c.domega_max;
-        omega_des[i] = (float)fmin(fmax(w, c.domega_min), c.domega_max);
-        if (tape) {
-            tape->fc[i] = (float)fc;
-            tape->dw_df[i] = (float)dw;
-            tape->in_f[i] = in_f;
-            tape->in_w[i] = in_w;
-        }
+        dfl f = df_mul(df_of(c.xAinv[i][0]), rhs[0]);
+#pragma unroll
+        for (int k = 1; k < 4; ++k) f = df_add(f, df_mul(df_of(c.xAinv[i][k]), rhs[k]));
+        rotor_command(c, i, f, omega_des, tape);
     }
 }
 
@@ -88,14 +142,20 @@ __device__ __forceinline__ void dcross(const double a[3], const double b[3], dou
 // CTBR: u0 -> collective thrust m a, u1..3 -> desired rates; P rate loop with
 // gyroscopic feed-forward -> desired moment (Sec. III-A; the action type of the
 // paper's examples, Sec. IV).
-__device__ __forceinline__ void ctbr_rhs(const DynConsts& c, const float Om_f[3], const float u[4], double rhs[4]) {
-    const double Om[3] = {Om_f[0], Om_f[1], Om_f[2]};
-    const double L[3] = {c.dJ[0] * Om[0], c.dJ[1] * Om[1], c.dJ[2] * Om[2]};
-    double gyro[3];
-    dcross(Om, L, gyro);
-    rhs[0] = ((double)u[0] + 1.0) * c.dhalf_a_max_m;
+__device__ __forceinline__ void ctbr_rhs(const DynConsts& c, const float Om[3], const float u[4], dfl rhs[4]) {
+    dfl L[3];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) rhs[j + 1] = c.dJK[j] * ((double)u[j + 1] * c.drate_max[j] - Om[j]) + gyro[j];
+    for (int j = 0; j < 3; ++j) L[j] = df_mul(df_of(c.xJ[j]), df_of(Om[j]));
+    // gyroscopic feed-forward Omega x (J Omega)
+    const dfl gyro[3] = {df_sub(df_mul(df_of(Om[1]), L[2]), df_mul(df_of(Om[2]), L[1])),
+                         df_sub(df_mul(df_of(Om[2]), L[0]), df_mul(df_of(Om[0]), L[2])),
+                         df_sub(df_mul(df_of(Om[0]), L[1]), df_mul(df_of(Om[1]), L[0]))};
+    rhs[0] = df_mul(df_two_sum(u[0], 1.0f), df_of(c.xhalf_a_max_m));
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        rhs[j + 1] = df_add(df_mul(df_of(c.xJK[j]),
+                                   df_sub(df_mul(df_of(u[j + 1]), df_of(c.xrate_max[j])), df_of(Om[j]))),
+                            gyro[j]);
 }
 
 // LV / PS (geometric control with yaw, after Lee et al. 2010): desired force
@@ -184,36 +244,23 @@ __device__ __forceinline__ void controller(const DynConsts& c, const float y[17]
                                            float omega_des[4], CtrlTape* tape) {
     if (c.controller == 1) {
         // SRT: u_i in [-1, 1] -> rotor i's thrust (u_i + 1) / 2 * f(omega_max)
-        const double fh = c.df_hi;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const double f = ((double)u[i] + 1.0) * 0.5 * fh;
-            const bool in_f = f >= c.df_lo && f <= c.df_hi;
-            const double fc = fmin(fmax(f, c.df_lo), c.df_hi);
-            double w, dw;
-            if (c.dk[2] != 0.0) {
-                const double disc = c.dk[1] * c.dk[1] - 4.0 * c.dk[2] * (c.dk[0] - fc);
-                const double sq = sqrt(fmax(disc, 0.0));
-                w = (sq - c.dk[1]) / (2.0 * c.dk[2]);
-                dw = disc > 0.0 ? 1.0 / sq : 0.0;
-            } else {
-                w = (fc - c.dk[0]) / c.dk[1];
-                dw = 1.0 / c.dk[1];
-            }
-            const bool in_w = w >= c.domega_min && w <= c.domega_max;
-            omega_des[i] = (float)fmin(fmax(w, c.domega_min), c.domega_max);
-            if (tape) {
-                tape->fc[i] = (float)fc;
-                tape->dw_df[i] = (float)dw;
-                tape->in_f[i] = in_f;
-                tape->in_w[i] = in_w;
-            }
-        }
+        for (int i = 0; i < 4; ++i)
+            rotor_command(c, i, df_mul(df_two_sum(u[i], 1.0f), df_of(c.xhalf_f_hi)), omega_des, tape);
         return;
     }
-    double rhs[4];
-    if (c.controller == 2 || c.controller == 3) geometric_rhs(c, y, u, c.controller == 3, rhs);
-    else ctbr_rhs(c, y + 10, u, rhs);
+    dfl rhs[4];
+    if (c.controller == 2 || c.controller == 3) {
+        double r[4];
+        geometric_rhs(c, y, u, c.controller == 3, r);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float hi = (float)r[j];
+            rhs[j] = {hi, (float)(r[j] - (double)hi)};
+        }
+    } else {
+        ctbr_rhs(c, y + 10, u, rhs);
+    }
     allocate(c, rhs, omega_des, tape);
 }
 
