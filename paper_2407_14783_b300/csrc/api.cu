@@ -14,11 +14,22 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "launch.h"
 #include "visfly_b300.h"
 
 using namespace vf;
+
+namespace {
+// NVTX range over one entry point (header-only NVTX: a no-op unless a
+// profiler is attached), so timelines show which library call ran when.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+}  // namespace
 
 namespace {
 
@@ -648,6 +659,7 @@ int sim_set_params(sim_ctx* c, const sim_params* p) {
 
 int sim_create_scene(sim_ctx* c, const float* verts, int64_t n_verts, const int32_t* tris, int64_t n_tris,
                      const uint8_t* rgb, int32_t* scene_id_out, void* stream) {
+    Range nvtx_range("sim_create_scene");
     if (!c || !scene_id_out) return fail(SIM_ERR_INVALID_ARG, "null argument");
     *scene_id_out = -1;
     if (n_verts < 0 || n_tris < 0 || n_tris > (1ll << 27) || n_verts > (1ll << 31))
@@ -755,6 +767,7 @@ int sim_scene_info_get(const sim_ctx* c, int32_t id, sim_scene_info* info) {
 }
 
 int sim_step(sim_ctx* c, int32_t n, float* state, const float* cmd, float* ckpt, void* stream) {
+    Range nvtx_range("sim_step");
     if (!c || n < 0 || (n > 0 && (!state || !cmd))) return fail(SIM_ERR_INVALID_ARG, "bad sim_step arguments");
     DeviceGuard g(c->device);
     cudaError_t e = launch_step(c->dyn, n, state, cmd, ckpt, (cudaStream_t)stream);
@@ -763,6 +776,7 @@ int sim_step(sim_ctx* c, int32_t n, float* state, const float* cmd, float* ckpt,
 
 int sim_step_backward(sim_ctx* c, int32_t n, const float* state_in, const float* cmd, const float* g_out,
                       float* g_in, float* g_cmd, void* stream) {
+    Range nvtx_range("sim_step_backward");
     if (!c || n < 0 || (n > 0 && (!state_in || !cmd || !g_out || !g_in || !g_cmd)))
         return fail(SIM_ERR_INVALID_ARG, "bad sim_step_backward arguments");
     if (c->dyn.controller > 1) return fail(SIM_ERR_INVALID_ARG, "the adjoint covers the CTBR and SRT controllers");
@@ -773,6 +787,7 @@ int sim_step_backward(sim_ctx* c, int32_t n, const float* state_in, const float*
 
 int sim_rollout(sim_ctx* c, int32_t n, int32_t T, int32_t K, const float* state0, const float* cmds, float* states_out,
                 float* ckpt, float* state_final, void* stream) {
+    Range nvtx_range("sim_rollout");
     if (!c || n < 0 || T < 0 || K < 1 || (n > 0 && (!state0 || (T > 0 && !cmds))))
         return fail(SIM_ERR_INVALID_ARG, "bad sim_rollout arguments");
     DeviceGuard g(c->device);
@@ -782,6 +797,7 @@ int sim_rollout(sim_ctx* c, int32_t n, int32_t T, int32_t K, const float* state0
 
 int sim_rollout_backward(sim_ctx* c, int32_t n, int32_t T, int32_t K, const float* ckpt, const float* cmds,
                          const float* g_states, float* g_state0, float* g_cmds, void* stream) {
+    Range nvtx_range("sim_rollout_backward");
     if (!c || n < 0 || T < 1 || K < 1 || K > kMaxCkptK ||
         (n > 0 && (!ckpt || !cmds || !g_states || !g_state0 || !g_cmds)))
         return fail(SIM_ERR_INVALID_ARG, "bad sim_rollout_backward arguments");
@@ -794,6 +810,7 @@ int sim_rollout_backward(sim_ctx* c, int32_t n, int32_t T, int32_t K, const floa
 
 int sim_render_ex(sim_ctx* c, int32_t n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb,
                   int32_t* hit, int32_t* seg, void* stream) {
+    Range nvtx_range("sim_render_ex");
     int rc = check_render_args(c, n, soa, state);
     if (rc) return rc;
     DeviceGuard g(c->device);
@@ -825,6 +842,7 @@ int sim_set_swarm(sim_ctx* c, const sim_swarm* cfg) {
 
 int sim_swarm_proximity(sim_ctx* c, int32_t n, const int32_t* soa, const float* state, float radius, float* dist,
                         int32_t* other, int32_t* n_collide, void* stream) {
+    Range nvtx_range("sim_swarm_proximity");
     int rc = check_render_args(c, n, soa, state);
     if (rc) return rc;
     if (!(radius >= 0.0f) || !std::isfinite(radius)) return fail(SIM_ERR_INVALID_ARG, "radius must be finite and >= 0");
@@ -913,6 +931,7 @@ int sim_scene_set_labels(sim_ctx* c, int32_t id, const int32_t* labels, int64_t 
 
 int sim_render_counted(sim_ctx* c, int32_t n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb,
                        int32_t* hit, sim_render_counters* out, void* stream) {
+    Range nvtx_range("sim_render_counted");
     int rc = check_render_args(c, n, soa, state);
     if (rc) return rc;
     if (!out) return fail(SIM_ERR_INVALID_ARG, "null counters");
@@ -938,6 +957,7 @@ int sim_render_counted(sim_ctx* c, int32_t n, const int32_t* soa, const float* s
 
 int sim_render_scene(sim_ctx* c, int32_t n, int32_t scene_id, const float* state, float* depth, uint8_t* rgb,
                      int32_t* hit, void* stream) {
+    Range nvtx_range("sim_render_scene");
     // a device array of n copies of scene_id is needed; keep a small cache in the context staging area
     if (!c) return fail(SIM_ERR_INVALID_ARG, "null context");
     if (scene_id < 0 || scene_id >= (int)c->scenes.size() || !c->scenes[scene_id].live)
@@ -976,6 +996,7 @@ void* direct_host_address(const void* p) {
 
 int sim_env_step(sim_ctx* c, int32_t n, const int32_t* soa, float* state, const float* cmd_host, float* depth_host,
                  uint8_t* rgb_host, float* state_host, void* stream) {
+    Range nvtx_range("sim_env_step");
     if (!c || n < 0 || (n > 0 && (!soa || !state || !cmd_host)))
         return fail(SIM_ERR_INVALID_ARG, "bad sim_env_step arguments");
     if (n == 0) return SIM_OK;
@@ -1138,6 +1159,7 @@ int sim_loop_create(sim_ctx* c, sim_loop** out, int32_t n, int32_t T, const int3
 }
 
 int sim_loop_launch(sim_loop* L, void* stream) {
+    Range nvtx_range("sim_loop_launch");
     if (!L || !L->exec) return fail(SIM_ERR_INVALID_ARG, "null loop");
     DeviceGuard g(L->ctx->device);
     cudaError_t e = cudaGraphLaunch(L->exec, (cudaStream_t)stream);
@@ -1174,6 +1196,7 @@ int sim_render_config_list(sim_render_config* out, int32_t max) { return render_
 
 int sim_autotune_render(sim_ctx* c, int32_t n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb,
                         int32_t iters, sim_render_config* best, float* times_ms, int32_t max_times, void* stream) {
+    Range nvtx_range("sim_autotune_render");
     int rc = check_render_args(c, n, soa, state);
     if (rc) return rc;
     if (iters < 1 || !best) return fail(SIM_ERR_INVALID_ARG, "bad autotune arguments");
@@ -1241,6 +1264,7 @@ int sim_autotune_render(sim_ctx* c, int32_t n, const int32_t* soa, const float* 
 
 int sim_nearest_obstacle(sim_ctx* c, int32_t n, const int32_t* soa, const float* state, float max_dist, float* dist,
                          float* point, int32_t* tri, void* stream) {
+    Range nvtx_range("sim_nearest_obstacle");
     if (!c || n < 0 || (n > 0 && (!soa || !state || !dist)) || !(max_dist > 0.0f))
         return fail(SIM_ERR_INVALID_ARG, "bad sim_nearest_obstacle arguments");
     if (n == 0) return SIM_OK;

@@ -177,3 +177,47 @@ def test_render_maximum_image_size(make_sim, oracle_mod, wl):
     compare_images(oracle_mod.Scene.from_workload(sc), p, s.astype(np.float64), d, c, h, max_tie_frac=0.02)
     with pytest.raises(Exception):
         make_sim(wl.params(width=1025, height=64))
+
+
+def test_bounded_status_wait_times_out_then_succeeds(make_sim, wl):
+    """sim_get_status gives up after its deadline while the stream is still busy
+    (SIM_ERR_TIMEOUT, nothing faults or hangs), and succeeds once it drains."""
+    from paper_2407_14783_b300.sim import to_soa
+    p = wl.params()
+    sc = wl.cluttered_scene()
+    sim = make_sim(p)
+    sid = sim.add_workload_scene(sc)
+    n = 4096
+    st = to_soa(wl.spawn_states(sc, n, 21, 1100.0).astype(np.float32))
+    ids = torch.full((n,), sid, dtype=torch.int32, device="cuda")
+    d, c, _ = sim.alloc_images(n)
+    torch.cuda.synchronize()
+    for _ in range(4):
+        sim.render(ids, st, d, c)            # a few milliseconds of queued work
+    rc = sim.status(timeout_ms=0)
+    assert rc == -6                           # SIM_ERR_TIMEOUT
+    assert sim.status(timeout_ms=60000) == 0
+    assert torch.isfinite(d).all()
+
+
+def test_outputs_finite_and_in_range(make_sim, wl):
+    """No NaN or Inf anywhere: depth in (0, max_depth], hit ids in range, and
+    the state after 100 steps of uniform commands."""
+    from paper_2407_14783_b300.sim import to_soa
+    p = wl.params()
+    sc = wl.cluttered_scene()
+    sim = make_sim(p)
+    sid = sim.add_workload_scene(sc)
+    n = 128
+    st = to_soa(wl.spawn_states(sc, n, 22, 1100.0).astype(np.float32))
+    cm = torch.from_numpy(np.ascontiguousarray(wl.uniform_commands(100, n, 23).transpose(0, 2, 1))).float().cuda()
+    for t in range(100):
+        sim.step(st, cm[t])
+    ids = torch.full((n,), sid, dtype=torch.int32, device="cuda")
+    d, c, h = sim.alloc_images(n, hit=True)
+    sim.render(ids, st, d, c, h)
+    torch.cuda.synchronize()
+    sim.check()
+    assert torch.isfinite(st).all()
+    assert torch.isfinite(d).all() and (d > 0).all() and (d <= p["max_depth"]).all()
+    assert ((h >= -1) & (h < sc.n_tris)).all()
