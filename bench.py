@@ -242,23 +242,6 @@ def raycast_roofline(sim, cnt, n, p, render_ms):
                                  * rays_per_item / (render_ms * 1e-3) / 1e9}
 
 
-def _core_speeds():
-    """Seconds of a short pure-Python loop on each core this process may use.
-    On shared hosts the cores differ several-fold and drift; the end-to-end loop
-    is timed under default scheduling (the reported value) and once more with
-    its thread pinned to the core that was fastest here."""
-    aff = sorted(os.sched_getaffinity(0))
-    out = {}
-    for c in aff:
-        os.sched_setaffinity(0, {c})
-        t = time.perf_counter()
-        for _ in range(3):
-            sum(range(20000))
-        out[c] = time.perf_counter() - t
-    os.sched_setaffinity(0, set(aff))
-    return out
-
-
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -338,10 +321,10 @@ def run_ours(args):
     rgb_h = torch.empty((n, p["height"], p["width"], 3), dtype=torch.uint8).pin_memory()
     K2 = min(K, 200)
     state.copy_(spawn)
-    def e2e_loop():
+    def e2e_loop(step):
         state.copy_(spawn)
         for t in range(3):
-            sim.env_step(ids, state, cmd_host[t], depth_h, rgb_h)
+            step(t)
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
@@ -349,7 +332,7 @@ def run_ours(args):
         for k in range(K2):
             if k % EPISODE == 0:
                 state.copy_(spawn)
-            sim.env_step(ids, state, cmd_host[W + k], depth_h, rgb_h)
+            step(W + k)
             stream.synchronize()        # the host reads the observation every step
         e2e_s = time.perf_counter() - t0
         if ws > 1:
@@ -358,21 +341,16 @@ def run_ours(args):
             e2e_s = float(t.item())
         return ws * n * K2 / e2e_s
 
-    unpinned = e2e_loop()
-    speeds = _core_speeds()
-    fast = min(speeds, key=speeds.get)
-    aff = os.sched_getaffinity(0)
-    os.sched_setaffinity(0, {fast})
-    try:
-        pinned = e2e_loop()
-    finally:
-        os.sched_setaffinity(0, aff)
-    e2e = {"value": unpinned, "unit": "agent-frames/s", "h2d_bytes_per_step": 4 * 4 * n,
+    # the prepared step (one captured graph per call) is the value; the one-shot
+    # sim_env_step call is reported beside it
+    env = sim.make_env(ids, state, depth_h, rgb_h)
+    prepared = e2e_loop(lambda t: env.step(cmd_host[t]))
+    env.close()
+    one_shot = e2e_loop(lambda t: sim.env_step(ids, state, cmd_host[t], depth_h, rgb_h))
+    e2e = {"value": prepared, "unit": "agent-frames/s", "h2d_bytes_per_step": 4 * 4 * n,
            "d2h_bytes_per_step": n * p["height"] * p["width"] * 7, "steps": K2,
-           "host_thread": "default scheduling (the value); pinned to the fastest core by a short Python loop: "
-                          f"value_pinned (core {fast}, {1e3 * speeds[fast]:.2f} ms vs median "
-                          f"{1e3 * statistics.median(speeds.values()):.2f} ms)",
-           "value_pinned": pinned}
+           "api": "Sim.make_env(...).step (sim_env_run) with page-locked host buffers",
+           "value_env_step": one_shot}
 
     # traversal counters of one launch -> algorithmic bytes of the ray-cast kernel
     state.copy_(spawn)

@@ -40,6 +40,12 @@
 extern "C" {
 #endif
 
+/* The library is built with hidden symbol visibility; the declarations below
+ * are its exported interface. */
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
 typedef struct sim_ctx sim_ctx;
 
 typedef enum {
@@ -300,6 +306,30 @@ int sim_rollout_backward(sim_ctx* ctx, int32_t n_agents, int32_t T, int32_t K, c
 int sim_env_step(sim_ctx* ctx, int32_t n_agents, const int32_t* scene_of_agent, float* state,
                  const float* cmd_host, float* depth_host, uint8_t* rgb_host, float* state_host, void* stream);
 
+/* A prepared environment step: sim_env_step for a fixed set of agents and
+ * fixed output buffers, validated once and then run as one captured CUDA graph
+ * per call (band-word reset, dynamics, render with the streamed download,
+ * optional state download), so a control loop pays one graph launch of host
+ * work per step instead of a series of launches and checks.
+ *   scene_of_agent dev int32 [n]; state dev [17][n] (updated in place by every
+ *   run); depth_host float32 [n][H][W], rgb_host uint8 [n][H][W][3] and
+ *   state_host float32 [17][n] are host buffers (at least one image buffer),
+ *   each NULL or page-locked (cudaHostAlloc, cudaMallocHost, cudaHostRegister);
+ *   INVALID_ARG otherwise.  All of them must stay allocated until
+ *   sim_env_destroy.
+ * sim_env_run: one step with commands cmd_host float32 [4][n] (page-locked:
+ *   read in place; pageable: copied first), asynchronous on `stream`; the host
+ *   buffers are complete when the stream reaches this point.  A later change of
+ *   the context's parameters, scenes, labels, render configuration, noise or
+ *   multi-agent mode is picked up by the next run (it synchronises `stream`
+ *   and captures anew).  The prepared step owns its staging, scheduling hints
+ *   and work counters, so it does not share them with other launches. */
+typedef struct sim_env sim_env;
+int sim_env_create(sim_ctx* ctx, sim_env** out, int32_t n_agents, const int32_t* scene_of_agent, float* state,
+                   float* depth_host, uint8_t* rgb_host, float* state_host);
+int sim_env_run(sim_env* env, const float* cmd_host, void* stream);
+int sim_env_destroy(sim_env* env);
+
 /* A captured step loop: T environment steps (sim_step then sim_render per
  * step, commands cmds[t]) recorded once into a CUDA graph and replayed with one
  * launch (the batched-multi-scene pattern: many scenes, one persistent render
@@ -423,6 +453,10 @@ int sim_probe_read_bandwidth(sim_ctx* ctx, size_t bytes, int32_t iters, double* 
 
 /* Library version string. */
 const char* sim_version(void);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
 
 #ifdef __cplusplus
 }

@@ -117,6 +117,9 @@ SIGNATURES = {
     "sim_scene_set_labels": [_vp, _i32, _vp, _i64],
     "sim_set_noise": [_vp, _vp],
     "sim_set_swarm": [_vp, _vp],
+    "sim_env_create": [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp],
+    "sim_env_run": [_vp, _vp, _vp],
+    "sim_env_destroy": [_vp],
     "sim_swarm_proximity": [_vp, _i32, _vp, _vp, ctypes.c_float, _vp, _vp, _vp, _vp],
     "sim_render_scene_static": [_vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp],
     "sim_step_backward": [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp],

@@ -19,7 +19,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-O3", "-lineinfo", "-std=c++17",
-    "-Xcompiler", "-fPIC,-O2",
+    "-Xcompiler", "-fPIC,-O2,-fvisibility=hidden",
     "-I" + INCLUDE, "-I" + CSRC,
 ]
 

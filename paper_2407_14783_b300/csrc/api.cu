@@ -67,6 +67,33 @@ struct sim_loop {
     vf::SwarmScratch swarm;  // the loop's own multi-agent buffers (baked into the graph)
 };
 
+// A prepared environment step (sim_env_create): its own buffers and one
+// captured graph of band-word reset, dynamics and render.
+struct sim_env {
+    sim_ctx* ctx = nullptr;
+    int n = 0;
+    const int32_t* soa = nullptr;
+    float* state = nullptr;
+    float* h_depth = nullptr;  // device addresses of the page-locked host images
+    uint8_t* h_rgb = nullptr;
+    float* h_state = nullptr;
+    float* d_depth = nullptr;  // render targets (device staging of the streamed download)
+    uint8_t* d_rgb = nullptr;
+    float* d_cmd = nullptr;    // commands from pageable host memory
+    unsigned* band = nullptr;
+    size_t band_words = 0, rows_max = 0;
+    unsigned* counters = nullptr;
+    void* sched_mem = nullptr;
+    int sched_cap = 0;
+    vf::SwarmScratch swarm;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t step_node = nullptr;
+    unsigned long long gen = 0;
+    const float* cmd_in_graph = nullptr;
+};
+
 struct sim_ctx {
     int device = 0;
     int num_sms = 0;
@@ -98,6 +125,9 @@ struct sim_ctx {
     uint8_t* d_rgb = nullptr;
     unsigned* d_band = nullptr;  // completion words of the streamed download
     size_t band_words = 0;
+    // bumped by every call that changes what a captured environment step
+    // launches (parameters, scenes, labels, render config, noise, swarm)
+    std::atomic<unsigned long long> generation{1};
     // multi-agent mode (sim_set_swarm) and its per-launch buffers
     bool swarm_on = false;
     sim_swarm swarm_cfg{};
@@ -646,6 +676,7 @@ int sim_destroy_ctx(sim_ctx* c) {
 
 int sim_set_params(sim_ctx* c, const sim_params* p) {
     if (!c || !p) return fail(SIM_ERR_INVALID_ARG, "null argument");
+    ++c->generation;
     DynConsts d;
     CamConsts cam;
     int rc = derive(*p, d, cam);
@@ -661,6 +692,7 @@ int sim_create_scene(sim_ctx* c, const float* verts, int64_t n_verts, const int3
                      const uint8_t* rgb, int32_t* scene_id_out, void* stream) {
     Range nvtx_range("sim_create_scene");
     if (!c || !scene_id_out) return fail(SIM_ERR_INVALID_ARG, "null argument");
+    ++c->generation;
     *scene_id_out = -1;
     if (n_verts < 0 || n_tris < 0 || n_tris > (1ll << 27) || n_verts > (1ll << 31))
         return fail(SIM_ERR_INVALID_ARG, "bad mesh size");
@@ -745,6 +777,7 @@ int sim_create_scene(sim_ctx* c, const float* verts, int64_t n_verts, const int3
 
 int sim_destroy_scene(sim_ctx* c, int32_t id) {
     if (!c) return fail(SIM_ERR_INVALID_ARG, "null context");
+    ++c->generation;
     std::lock_guard<std::mutex> lk(c->mu);
     if (id < 0 || id >= (int)c->scenes.size() || !c->scenes[id].live) return fail(SIM_ERR_NOT_FOUND, "no such scene");
     DeviceGuard g(c->device);
@@ -827,6 +860,7 @@ int sim_render(sim_ctx* c, int32_t n, const int32_t* soa, const float* state, fl
 
 int sim_set_swarm(sim_ctx* c, const sim_swarm* cfg) {
     if (!c) return fail(SIM_ERR_INVALID_ARG, "null context");
+    ++c->generation;
     if (cfg) {
         for (int k = 0; k < 3; ++k)
             if (!(cfg->half[k] > 0.0f) || !std::isfinite(cfg->half[k]))
@@ -862,6 +896,7 @@ int sim_swarm_proximity(sim_ctx* c, int32_t n, const int32_t* soa, const float* 
 
 int sim_set_noise(sim_ctx* c, const sim_noise* cfg) {
     if (!c) return fail(SIM_ERR_INVALID_ARG, "null context");
+    ++c->generation;
     NoiseParams np{};
     unsigned long long frame = 0;
     if (cfg) {
@@ -907,6 +942,7 @@ int sim_set_noise(sim_ctx* c, const sim_noise* cfg) {
 
 int sim_scene_set_labels(sim_ctx* c, int32_t id, const int32_t* labels, int64_t n) {
     if (!c) return fail(SIM_ERR_INVALID_ARG, "null context");
+    ++c->generation;
     std::lock_guard<std::mutex> lk(c->mu);
     if (id < 0 || id >= (int)c->scenes.size() || !c->scenes[id].live) return fail(SIM_ERR_NOT_FOUND, "no such scene");
     SceneRec& r = c->scenes[id];
@@ -984,7 +1020,7 @@ int sim_render_scene(sim_ctx* c, int32_t n, int32_t scene_id, const float* state
 // Device address of a host buffer that kernels can reach directly (page-locked
 // host memory under unified addressing: cudaHostAlloc, cudaMallocHost or
 // cudaHostRegister), else null (pageable memory goes through staging copies).
-void* direct_host_address(const void* p) {
+static void* direct_host_address(const void* p) {
     if (!p) return nullptr;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -1091,6 +1127,181 @@ int sim_env_step(sim_ctx* c, int32_t n, const int32_t* soa, float* state, const 
     return e == cudaSuccess ? SIM_OK : cuda_fail(e, "observation download");
 }
 
+// ------------------------------------------------------------ prepared step
+namespace {
+
+void env_free(sim_env* E) {
+    sim_ctx* c = E->ctx;
+    if (E->exec) cudaGraphExecDestroy(E->exec);
+    if (E->graph) cudaGraphDestroy(E->graph);
+    E->exec = nullptr;
+    E->graph = nullptr;
+    const size_t px = (size_t)E->n * c->cam.W * c->cam.H;
+    ctx_free(c, E->d_depth, sizeof(float) * px);
+    ctx_free(c, E->d_rgb, 3 * px);
+    ctx_free(c, E->d_cmd, sizeof(float) * 4 * (size_t)E->n);
+    ctx_free(c, E->band, sizeof(unsigned) * E->band_words);
+    ctx_free(c, E->counters, 2 * sizeof(unsigned));
+    if (E->sched_mem) ctx_free(c, E->sched_mem, sched_bytes_for(E->sched_cap));
+    swarm_free(c, E->swarm);
+    if (E->cap) cudaStreamDestroy(E->cap);
+}
+
+// (Re)capture the step graph: band-word reset, dynamics, render with the
+// streamed download, and the optional state download.  The caller has made
+// sure nothing of an earlier capture is still running.
+int env_capture(sim_env* E, const float* cmd) {
+    sim_ctx* c = E->ctx;
+    if (E->exec) cudaGraphExecDestroy(E->exec);
+    if (E->graph) cudaGraphDestroy(E->graph);
+    E->exec = nullptr;
+    E->graph = nullptr;
+    const unsigned long long gen = c->generation.load();
+    int rc = check_render_args(c, E->n, E->soa, E->state);
+    if (rc) return rc;
+    const sim_render_config cfg = c->rcfg;
+    const long long items = render_items(c, E->n, cfg);
+    if (items > E->sched_cap) {
+        if (E->sched_mem) ctx_free(c, E->sched_mem, sched_bytes_for(E->sched_cap));
+        E->sched_mem = nullptr;
+        E->sched_cap = 0;
+        if ((rc = sched_alloc(c, (int)items, &E->sched_mem, E->cap))) return rc;
+        E->sched_cap = (int)items;
+    }
+    if (c->swarm_on) {
+        int rows;
+        {
+            std::lock_guard<std::mutex> lk(c->mu);
+            rows = (int)c->scenes.size();
+        }
+        if ((rc = swarm_reserve(c, E->swarm, E->n, rows))) return rc;
+    }
+    cudaError_t e = cudaStreamSynchronize(E->cap);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(E->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "environment capture");
+    e = cudaMemsetAsync(E->band, 0, sizeof(unsigned) * E->band_words, E->cap);
+    if (e == cudaSuccess) e = launch_step(c->dyn, E->n, E->state, cmd, nullptr, E->cap);
+    if (e == cudaSuccess) {
+        // the node just added is the dynamics kernel: its command argument is
+        // rebound per call without a new capture
+        cudaStreamCaptureStatus st;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        e = cudaStreamGetCaptureInfo(E->cap, &st, nullptr, nullptr, &deps, nullptr, &nd);
+        E->step_node = (e == cudaSuccess && nd == 1) ? deps[0] : nullptr;
+        if (e == cudaSuccess && !E->step_node) e = cudaErrorUnknown;
+    }
+    if (e == cudaSuccess)
+        rc = do_render(c, E->n, E->soa, E->state, E->d_depth, E->d_rgb, nullptr, false, cfg, E->cap, E->counters,
+                       E->sched_mem, E->sched_cap, nullptr, E->h_depth, E->h_rgb, E->band,
+                       E->band + (size_t)E->n * E->rows_max, c->swarm_on ? SwarmUse::own : SwarmUse::none,
+                       &E->swarm);
+    if (e == cudaSuccess && rc == SIM_OK && E->h_state)
+        e = cudaMemcpyAsync(E->h_state, E->state, sizeof(float) * vf::kStateDim * E->n, cudaMemcpyDeviceToHost,
+                            E->cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(E->cap, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess && rc == SIM_OK) e = cudaGraphInstantiate(&E->exec, g, 0);
+    E->graph = g;
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "environment capture");
+    E->gen = gen;
+    E->cmd_in_graph = cmd;
+    return SIM_OK;
+}
+
+}  // namespace
+
+int sim_env_create(sim_ctx* c, sim_env** out, int32_t n, const int32_t* soa, float* state, float* depth_host,
+                   uint8_t* rgb_host, float* state_host) {
+    Range nvtx_range("sim_env_create");
+    if (!out) return fail(SIM_ERR_INVALID_ARG, "null output");
+    *out = nullptr;
+    int rc = check_render_args(c, n, soa, state);
+    if (rc) return rc;
+    if (n < 1 || (!depth_host && !rgb_host)) return fail(SIM_ERR_INVALID_ARG, "need agents and an image buffer");
+    float* hd = depth_host ? (float*)direct_host_address(depth_host) : nullptr;
+    uint8_t* hr = rgb_host ? (uint8_t*)direct_host_address(rgb_host) : nullptr;
+    if ((depth_host && !hd) || (rgb_host && !hr) || (state_host && !direct_host_address(state_host)))
+        return fail(SIM_ERR_INVALID_ARG, "the host buffers of a prepared step must be page-locked");
+    DeviceGuard g(c->device);
+    sim_env* E = new sim_env();
+    E->ctx = c;
+    E->n = n;
+    E->soa = soa;
+    E->state = state;
+    E->h_depth = hd;
+    E->h_rgb = hr;
+    E->h_state = state_host;
+    const size_t px = (size_t)n * c->cam.W * c->cam.H;
+    E->rows_max = (size_t)c->cam.H;
+    E->band_words = (size_t)n * (E->rows_max + (size_t)((c->cam.W + 3) / 4) * ((c->cam.H + 1) / 2));
+    void* p = nullptr;
+    if ((depth_host && (rc = ctx_alloc(c, sizeof(float) * px, &p)) == SIM_OK)) E->d_depth = (float*)p;
+    if (!rc && rgb_host && (rc = ctx_alloc(c, 3 * px, &p)) == SIM_OK) E->d_rgb = (uint8_t*)p;
+    if (!rc && (rc = ctx_alloc(c, sizeof(float) * 4 * (size_t)n, &p)) == SIM_OK) E->d_cmd = (float*)p;
+    if (!rc && (rc = ctx_alloc(c, sizeof(unsigned) * E->band_words, &p)) == SIM_OK) E->band = (unsigned*)p;
+    if (!rc && (rc = ctx_alloc(c, 2 * sizeof(unsigned), &p)) == SIM_OK) E->counters = (unsigned*)p;
+    cudaError_t e = cudaSuccess;
+    if (!rc) e = cudaStreamCreateWithFlags(&E->cap, cudaStreamNonBlocking);
+    if (!rc && e == cudaSuccess) e = cudaMemsetAsync(E->counters, 0, 2 * sizeof(unsigned), E->cap);
+    if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(E->cap);
+    if (!rc && e != cudaSuccess) rc = cuda_fail(e, "environment set-up");
+    if (rc) {
+        env_free(E);
+        delete E;
+        return rc;
+    }
+    *out = E;
+    return SIM_OK;
+}
+
+int sim_env_run(sim_env* E, const float* cmd_host, void* stream) {
+    Range nvtx_range("sim_env_run");
+    if (!E || !cmd_host) return fail(SIM_ERR_INVALID_ARG, "null argument");
+    sim_ctx* c = E->ctx;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const float* cmd = (const float*)direct_host_address(cmd_host);
+    cudaError_t e = cudaSuccess;
+    if (!cmd) {
+        e = cudaMemcpyAsync(E->d_cmd, cmd_host, sizeof(float) * 4 * (size_t)E->n, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "command upload");
+        cmd = E->d_cmd;
+    }
+    if (!E->exec || E->gen != c->generation.load()) {
+        // the previous graph and the env's buffers must be idle before a new capture
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "environment step");
+        const int rc = env_capture(E, cmd);
+        if (rc) return rc;
+    } else if (cmd != E->cmd_in_graph) {
+        cudaKernelNodeParams kp;
+        e = cudaGraphKernelNodeGetParams(E->step_node, &kp);
+        if (e == cudaSuccess) {
+            void* args[5];
+            for (int k = 0; k < 5; ++k) args[k] = kp.kernelParams[k];
+            args[vf::kStepCmdArg] = &cmd;
+            kp.kernelParams = args;
+            e = cudaGraphExecKernelNodeSetParams(E->exec, E->step_node, &kp);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "command rebind");
+        E->cmd_in_graph = cmd;
+    }
+    e = cudaGraphLaunch(E->exec, s);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e, "environment step");
+}
+
+int sim_env_destroy(sim_env* E) {
+    if (!E) return SIM_OK;
+    DeviceGuard g(E->ctx->device);
+    cudaDeviceSynchronize();
+    env_free(E);
+    delete E;
+    return SIM_OK;
+}
+
 int sim_loop_create(sim_ctx* c, sim_loop** out, int32_t n, int32_t T, const int32_t* soa, float* state,
                     const float* cmds, float* depth, uint8_t* rgb, int32_t n_frames, void* stream) {
     if (!out) return fail(SIM_ERR_INVALID_ARG, "null output");
@@ -1189,6 +1400,7 @@ int sim_set_render_config(sim_ctx* c, const sim_render_config* cfg) {
     if (!c || !cfg) return fail(SIM_ERR_INVALID_ARG, "null argument");
     if (!render_config_valid(*cfg)) return fail(SIM_ERR_INVALID_ARG, "unsupported render configuration");
     c->rcfg = *cfg;
+    ++c->generation;
     return SIM_OK;
 }
 
@@ -1199,6 +1411,7 @@ int sim_autotune_render(sim_ctx* c, int32_t n, const int32_t* soa, const float* 
     Range nvtx_range("sim_autotune_render");
     int rc = check_render_args(c, n, soa, state);
     if (rc) return rc;
+    ++c->generation;
     if (iters < 1 || !best) return fail(SIM_ERR_INVALID_ARG, "bad autotune arguments");
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;

@@ -9,6 +9,9 @@ namespace vf {
 
 // dynamics.cu
 cudaError_t launch_step(const DynConsts& c, int n, float* state, const float* cmd, float* ckpt, cudaStream_t s);
+// Position of the command pointer among the dynamics kernel's arguments
+// (DynConsts, n, state, cmd, ckpt): a captured step rebinds it per call.
+constexpr int kStepCmdArg = 3;
 cudaError_t launch_step_backward(const DynConsts& c, int n, const float* state_in, const float* cmd,
                                  const float* g_out, float* g_in, float* g_cmd, cudaStream_t s);
 cudaError_t launch_rollout(const DynConsts& c, int n, int T, int K, const float* state0, const float* cmds,

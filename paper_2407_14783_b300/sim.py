@@ -302,6 +302,22 @@ class Sim:
         if rc:
             B.check(rc, "sim_env_step", self.h)
 
+    def make_env(self, scene_of_agent, state, depth_host=None, rgb_host=None, state_host=None) -> "Env":
+        """A prepared environment step over fixed agents and page-locked host
+        buffers (see sim_env_create): Env.step(cmd_host) runs one step."""
+        n = state.shape[1]
+        _need(scene_of_agent, torch.int32, (n,), "scene_of_agent")
+        _need(state, torch.float32, (STATE_DIM, n), "state")
+        for t, name, shape in ((depth_host, "depth_host", (n, self.H, self.W)),
+                               (rgb_host, "rgb_host", (n, self.H, self.W, 3)), (state_host, "state_host", (STATE_DIM, n))):
+            if t is not None and (t.is_cuda or not t.is_contiguous() or tuple(t.shape) != shape):
+                raise ValueError(f"{name}: need a contiguous host tensor of shape {shape}")
+        h = ctypes.c_void_p()
+        rc = self.L.sim_env_create(self.h, ctypes.byref(h), n, _ptr(scene_of_agent), _ptr(state), _ptr(depth_host),
+                                   _ptr(rgb_host), _ptr(state_host))
+        B.check(rc, "sim_env_create", self.h)
+        return Env(self, h, n, (scene_of_agent, state, depth_host, rgb_host, state_host))
+
     # ------------------------------------------------------------ status
     def status(self, timeout_ms: int = 10000, stream=None) -> int:
         return int(self.L.sim_get_status(self.h, _stream(stream), timeout_ms))
@@ -319,6 +335,34 @@ class Sim:
         B.check(self.L.sim_probe_read_bandwidth(self.h, nbytes, iters, ctypes.byref(g), _stream(stream)),
                 "sim_probe_read_bandwidth", self.h)
         return g.value
+
+
+class Env:
+    """A prepared environment step (see Sim.make_env); keeps its buffers alive."""
+
+    def __init__(self, sim, h, n, keep):
+        self.sim, self.h, self.n, self._keep = sim, h, n, keep
+        self._run = sim.L.sim_env_run
+
+    def step(self, cmd_host, stream=None):
+        """One environment step with host commands float32 [4, n]."""
+        if cmd_host.is_cuda or not cmd_host.is_contiguous() or cmd_host.numel() != 4 * self.n:
+            raise ValueError("cmd_host: need a contiguous host tensor of 4 * n floats")
+        s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        rc = self._run(self.h, cmd_host.data_ptr(), s)
+        if rc:
+            B.check(rc, "sim_env_run", self.sim.h)
+
+    def close(self):
+        if self.h and self.h.value:
+            self.sim.L.sim_env_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Loop:

@@ -138,3 +138,62 @@ def test_env_step_after_image_size_grows(make_sim, wl, pinned):
         sim.render(ids, st2, d, c)
         torch.cuda.synchronize()
         assert torch.equal(d_h, d.cpu()) and torch.equal(c_h, c.cpu())
+
+
+@pytest.mark.parametrize("cmd_pinned", [True, False])
+def test_prepared_env_equals_device_step_and_render(make_sim, wl, cmd_pinned):
+    """sim_env_run (one captured graph per step, the command pointer rebound
+    per call) gives exactly the step + render of device buffers, and the state
+    download."""
+    p, sim, ids, s0, cmds = _case(make_sim, wl)
+    n = s0.shape[1]
+    ref = _device_run(sim, ids, s0, cmds)
+    st = s0.clone()
+    depth_h = torch.full((n, p["height"], p["width"]), -7.0).pin_memory()
+    rgb_h = torch.full((n, p["height"], p["width"], 3), 9, dtype=torch.uint8).pin_memory()
+    state_h = torch.zeros((17, n)).pin_memory()
+    env = sim.make_env(ids, st, depth_h, rgb_h, state_h)
+    cmd_h = cmds.contiguous()
+    if cmd_pinned:
+        cmd_h = cmd_h.pin_memory()
+    for t in range(cmds.shape[0]):
+        env.step(cmd_h[t])
+        torch.cuda.current_stream().synchronize()
+        d, c, s = ref[t]
+        assert torch.equal(depth_h, d) and torch.equal(rgb_h, c) and torch.equal(state_h, s)
+    sim.check()
+    env.close()
+
+
+def test_prepared_env_picks_up_context_changes(make_sim, wl):
+    """A change of noise, render configuration or multi-agent mode between runs
+    is captured anew: the next run matches the device path under the new
+    settings."""
+    p, sim, ids, s0, cmds = _case(make_sim, wl, n=24)
+    n = s0.shape[1]
+    depth_h = torch.zeros((n, p["height"], p["width"])).pin_memory()
+    rgb_h = torch.zeros((n, p["height"], p["width"], 3), dtype=torch.uint8).pin_memory()
+    st = s0.clone()
+    env = sim.make_env(ids, st, depth_h, rgb_h)
+    noise = {"seed": 8, "first_frame": 3, "depth_gauss": 0.01, "rgb_gauss": 2.0}
+    cfg = sim.render_config()
+    changes = [lambda: sim.set_noise(noise), lambda: sim.set_noise(None),
+               lambda: sim.set_render_config(dict(cfg, tile_w=16, tile_h=2)),
+               lambda: sim.set_swarm((0.25, 0.18, 0.06), (250, 20, 30), 7)]
+    for apply in changes:
+        apply()
+        ref = _device_run(sim, ids, s0, cmds[:1])
+        apply()            # noise: back to its first frame, so both renders draw the same frame
+        st.copy_(s0)
+        env.step(cmds[0].contiguous().pin_memory())
+        torch.cuda.synchronize()
+        sim.check()
+        assert torch.equal(depth_h, ref[0][0]) and torch.equal(rgb_h, ref[0][1])
+    env.close()
+
+
+def test_prepared_env_rejects_pageable_images(make_sim, wl):
+    from paper_2407_14783_b300.binding import SimError
+    p, sim, ids, s0, cmds = _case(make_sim, wl, n=4)
+    with pytest.raises(SimError):
+        sim.make_env(ids, s0.clone(), torch.zeros((4, p["height"], p["width"])))
