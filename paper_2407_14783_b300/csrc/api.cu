@@ -437,9 +437,13 @@ int check_render_args(sim_ctx* c, int n, const void* soa, const void* state) {
     return SIM_OK;
 }
 
-// Scheduling hints: 8 header words, two heavy-item lists of cap entries and one
-// mark per item (see RenderArgs).  Zeroed at allocation.
-size_t sched_bytes_for(int cap) { return 64 + 2 * sizeof(unsigned) * (size_t)cap + sizeof(unsigned long long) * cap; }
+// Scheduling hints: a header (kSchedHeaderWords words), kBuckets item lists of
+// cap entries for each of the two slots, one mark and one quarter accumulator
+// per item.  Zeroed at allocation.
+size_t sched_bytes_for(int cap) {
+    return sizeof(unsigned long long) * kSchedHeaderWords + 2 * kBuckets * sizeof(unsigned) * (size_t)cap +
+           sizeof(unsigned long long) * cap + sizeof(unsigned) * (size_t)cap;
+}
 
 int sched_alloc(sim_ctx* c, int cap, void** mem, cudaStream_t s) {
     int rc = ctx_alloc(c, sched_bytes_for(cap), mem);
@@ -451,8 +455,12 @@ int sched_alloc(sim_ctx* c, int cap, void** mem, cudaStream_t s) {
 void sched_attach(RenderArgs& a, void* mem, int cap) {
     char* p = (char*)mem;
     a.sched = (unsigned long long*)p;
-    a.heavy = (unsigned*)(p + 64);
-    a.done = (unsigned long long*)(p + 64 + 2 * sizeof(unsigned) * (size_t)cap);
+    p += sizeof(unsigned long long) * kSchedHeaderWords;
+    a.heavy = (unsigned*)p;
+    p += 2 * kBuckets * sizeof(unsigned) * (size_t)cap;
+    a.done = (unsigned long long*)p;
+    p += sizeof(unsigned long long) * (size_t)cap;
+    a.acc = (unsigned*)p;
     a.sched_cap = cap;
 }
 

@@ -38,6 +38,12 @@ cudaError_t lbvh_build(int64_t nt, const float* d_verts, const int* d_tris, cons
                        LbvhAlloc alloc, void* alloc_user, LbvhResult* out, cudaStream_t s);
 
 // raycast.cu
+constexpr int kBuckets = 4;       // cost buckets of the longest-first schedule
+constexpr int kSchedEpoch = 2;    // header words of the scheduling state
+constexpr int kSchedTotal = 3;
+constexpr int kSchedLen = 4;      // kSchedLen .. kSchedLen + 2 * kBuckets - 1
+constexpr int kSchedHeaderWords = 16;
+
 struct RenderArgs {
     int n_agents;
     const int* scene_of_agent;
@@ -53,14 +59,16 @@ struct RenderArgs {
     int* err;
     long long* counters; // traversal counters (COUNT builds)
     // Longest-first scheduling state carried between launches (may be null):
-    // sched[0..1] cost sums, sched[2..3] heavy-list lengths, sched[4] epoch,
-    // sched[5] item count of the launch that wrote the lists, sched[6..7]
-    // split-list lengths; heavy[2][cap] item lists (heavy items from the front,
-    // very heavy ones to split from the back, each at most cap / 2); done[cap]
-    // marks of items already rendered in this launch.
+    // sched[0..1] cost sums of the two slots, sched[kSchedEpoch] epoch (its low
+    // bit is this launch's read slot), sched[kSchedTotal] item count of the
+    // launch that filed the buckets, sched[kSchedLen + slot * kBuckets + b]
+    // bucket lengths; heavy[slot][b][cap] the bucket lists; done[cap] marks of
+    // items already rendered in this launch; acc[cap] cost sums and arrival
+    // counts of split tiles' quarters (zero between launches).
     unsigned long long* sched;
     unsigned* heavy;
     unsigned long long* done;
+    unsigned* acc;
     int sched_cap;
     unsigned launch_id;  // distinct per host-side launch
     int32_t* seg;        // segmentation image [n][H][W] or null

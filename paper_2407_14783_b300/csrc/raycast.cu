@@ -225,54 +225,65 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                     asm volatile("prefetch.global.L2 [%0];" ::"l"(bases[k] + off));
         }
     }
-    // Longest-first order: tiles that cost more than twice the mean in the
-    // previous launch (same item count) are handed out first, then all others.
+    // Longest-first order from the previous launch with the same item count:
+    // its tiles were filed into cost buckets (over 4, 2, 1.25 and 0.8 times the
+    // mean cost); this launch hands out bucket 0 first, each tile as kSplit
+    // quarter-tile sub-packets on separate warps (a quarter walks only its own
+    // rays' paths, which shortens the longest dependent chain of node fetches),
+    // then buckets 1-3 whole, then every tile not yet rendered in natural order.
     const bool sched = A.sched != nullptr && total <= A.sched_cap;
-    unsigned long long mark = 0;
-    unsigned n_heavy = 0;
-    float thr = 0.0f;
-    int rd = 0;
-    unsigned n_split = 0;
-    if (sched) {
-        const unsigned ep = (unsigned)A.sched[4];
-        rd = ep & 1;
-        mark = ((unsigned long long)A.launch_id << 32) | ep;
-        if ((long long)A.sched[5] == total) {
-            const unsigned long long half = (unsigned long long)(A.sched_cap / 2);
-            n_split = (unsigned)min(min((unsigned long long)total, half), A.sched[6 + rd]);
-            n_heavy = (unsigned)min(min((unsigned long long)total - n_split, half), A.sched[2 + rd]);
-            thr = 2.0f * (float)A.sched[rd] / (float)total;
-        }
-    }
     // Splitting pays only when the launch is short enough for its longest tile
     // to matter: at most 12 tiles per resident warp.
     const bool allow_split = total <= 12ll * gridDim.x * kWarpsPerCta;
-    if (!allow_split) n_split = 0;
-    // Very heavy tiles (over twice the heavy threshold; a few per launch) run
-    // first, each as kSplit quarter-tile sub-packets on separate warps: a quarter
-    // walks only its own rays' paths, which shortens the longest dependent chain
-    // of node fetches.  Then the other heavy tiles, then the rest.
-    const long long n_first = (long long)n_split * kSplit;
+    __shared__ long long s_end[kBuckets];  // cumulative ends of the buckets in the counter's range
+    __shared__ float s_mean;
+    unsigned long long mark = 0;
+    int rd = 0;
+    if (sched) {
+        const unsigned ep = (unsigned)A.sched[kSchedEpoch];
+        rd = ep & 1;
+        mark = ((unsigned long long)A.launch_id << 32) | ep;
+        if (threadIdx.x == 0) {
+            const bool valid = (long long)A.sched[kSchedTotal] == total;
+            long long end = 0;
+            for (int b = 0; b < kBuckets; ++b) {
+                const long long len = valid ? (long long)min(A.sched[kSchedLen + rd * kBuckets + b],
+                                                            (unsigned long long)total)
+                                            : 0ll;
+                end += (b == 0 && allow_split) ? len * kSplit : len;
+                s_end[b] = end;
+            }
+            s_mean = valid ? (float)A.sched[rd] / (float)total : 0.0f;
+        }
+    } else if (threadIdx.x == 0) {
+        for (int b = 0; b < kBuckets; ++b) s_end[b] = 0;
+        s_mean = 0.0f;
+    }
+    __syncthreads();
+    const float mean = s_mean;
     for (;;) {
         long long item = 0;
         int sub = -1;
         if (lane == 0) {
             const long long k = (long long)atomicAdd(A.counter, 1u);
-            if (k < n_first) {
-                // split list: stored from the end of the heavy array
-                item = A.heavy[(size_t)rd * A.sched_cap + (A.sched_cap - 1 - k / kSplit)];
-                sub = (int)(k % kSplit);
-            } else if (k < n_first + (long long)n_heavy) {
-                item = A.heavy[(size_t)rd * A.sched_cap + (k - n_first)];
-            } else {
-                item = k - n_first - n_heavy;
-                if (sched && item < total && __ldcg(A.done + item) == mark) item = -1;  // done in the first pass
-                if (item >= total) item = total;                                      // no work left
-            }
-            // an entry from a concurrent launch of another size may not fit this one
-            if (k < n_first + (long long)n_heavy) {
+            if (k < s_end[kBuckets - 1]) {
+                int b = 0;
+                while (k >= s_end[b]) ++b;
+                const long long j = k - (b == 0 ? 0ll : s_end[b - 1]);
+                const unsigned* list = A.heavy + ((size_t)rd * kBuckets + b) * A.sched_cap;
+                if (b == 0 && allow_split) {
+                    item = list[j / kSplit];
+                    sub = (int)(j % kSplit);
+                } else {
+                    item = list[j];
+                }
+                // an entry from a concurrent launch of another size may not fit this one
                 if (item < total) __stcg(A.done + item, mark);
                 else item = -1;
+            } else {
+                item = k - s_end[kBuckets - 1];
+                if (sched && item < total && __ldcg(A.done + item) == mark) item = -1;  // done from a bucket
+                if (item >= total) item = total;                                      // no work left
             }
         }
         item = __shfl_sync(kFull, item, 0);
@@ -711,18 +722,30 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
         }
         if (COUNT) ++c_items;
         if (sched && lane == 0) {
+            // file this tile for the next launch by its cost; a split tile is
+            // judged by the sum of its quarters, by the quarter that completes it
             const int wr = rd ^ 1;
             atomicAdd(&A.sched[wr], (unsigned long long)item_cost);
-            // a split tile is judged by its first quarter, scaled to the whole tile
-            const float est = sub < 0 ? (float)item_cost : (float)(item_cost * kSplit);
-            if (thr > 0.0f && sub <= 0 && est > thr) {
-                if (allow_split && est > 2.0f * thr) {
-                    const unsigned long long k = atomicAdd(&A.sched[6 + wr], 1ull);
-                    if (k < (unsigned long long)A.sched_cap / 2)
-                        A.heavy[(size_t)wr * A.sched_cap + (A.sched_cap - 1 - k)] = (unsigned)item;
-                } else {
-                    const unsigned long long k = atomicAdd(&A.sched[2 + wr], 1ull);
-                    if (k < (unsigned long long)A.sched_cap / 2) A.heavy[(size_t)wr * A.sched_cap + k] = (unsigned)item;
+            unsigned est = 0;
+            bool judge = false;
+            if (sub < 0) {
+                est = (unsigned)item_cost;
+                judge = true;
+            } else {
+                const unsigned old = atomicAdd(A.acc + item, (unsigned)item_cost | (1u << 24));
+                if ((old >> 24) == (unsigned)(kSplit - 1)) {
+                    est = (old & 0xFFFFFFu) + (unsigned)item_cost;
+                    A.acc[item] = 0u;
+                    judge = true;
+                }
+            }
+            if (judge && mean > 0.0f) {
+                const float e = (float)est;
+                const int b = e > 4.0f * mean ? 0 : e > 2.0f * mean ? 1 : e > 1.25f * mean ? 2 : e > 0.8f * mean ? 3 : -1;
+                if (b >= 0) {
+                    const unsigned long long k = atomicAdd(&A.sched[kSchedLen + wr * kBuckets + b], 1ull);
+                    if (k < (unsigned long long)A.sched_cap)
+                        A.heavy[((size_t)wr * kBuckets + b) * A.sched_cap + k] = (unsigned)item;
                 }
             }
         }
@@ -756,10 +779,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
             if (sched) {
                 // this launch's read slot becomes the next launch's write slot
                 A.sched[rd] = 0ull;
-                A.sched[2 + rd] = 0ull;
-                A.sched[6 + rd] = 0ull;
-                A.sched[5] = (unsigned long long)total;
-                A.sched[4] = A.sched[4] + 1ull;
+                for (int b = 0; b < kBuckets; ++b) A.sched[kSchedLen + rd * kBuckets + b] = 0ull;
+                A.sched[kSchedTotal] = (unsigned long long)total;
+                A.sched[kSchedEpoch] = A.sched[kSchedEpoch] + 1ull;
             }
             __threadfence();
         }
