@@ -232,6 +232,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
     // rays' paths, which shortens the longest dependent chain of node fetches),
     // then buckets 1-3 whole, then every tile not yet rendered in natural order.
     const bool sched = A.sched != nullptr && total <= A.sched_cap;
+    // A launch that streams its bands to the host interleaves buckets 1-3 with
+    // natural-order items one for one: a band is complete only when all its
+    // tiles are, so taking every bucket first would hold back the download
+    // until late in the launch.  Both sides claim a tile by exchanging its
+    // done mark, so no tile is rendered twice.
+    const bool weave = EXTRA && sched && A.band_done != nullptr;
     // Splitting pays only when the launch is short enough for its longest tile
     // to matter: at most 12 tiles per resident warp.
     const bool allow_split = total <= 12ll * gridDim.x * kWarpsPerCta;
@@ -266,10 +272,26 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
         int sub = -1;
         if (lane == 0) {
             const long long k = (long long)atomicAdd(A.counter, 1u);
-            if (k < s_end[kBuckets - 1]) {
+            // position in the bucket lists, or -1 for a natural-order item at nat
+            long long kb = -1, nat = 0;
+            if (!weave) {
+                if (k < s_end[kBuckets - 1]) kb = k;
+                else nat = k - s_end[kBuckets - 1];
+            } else if (k < s_end[0]) {
+                kb = k;
+            } else {
+                const long long r = k - s_end[0], pair = s_end[kBuckets - 1] - s_end[0];
+                if (r < 2 * pair) {
+                    if (r & 1) nat = r >> 1;
+                    else kb = s_end[0] + (r >> 1);
+                } else {
+                    nat = r - pair;
+                }
+            }
+            if (kb >= 0) {
                 int b = 0;
-                while (k >= s_end[b]) ++b;
-                const long long j = k - (b == 0 ? 0ll : s_end[b - 1]);
+                while (kb >= s_end[b]) ++b;
+                const long long j = kb - (b == 0 ? 0ll : s_end[b - 1]);
                 const unsigned* list = A.heavy + ((size_t)rd * kBuckets + b) * A.sched_cap;
                 if (b == 0 && allow_split) {
                     item = list[j / kSplit];
@@ -278,12 +300,18 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                     item = list[j];
                 }
                 // an entry from a concurrent launch of another size may not fit this one
-                if (item < total) __stcg(A.done + item, mark);
-                else item = -1;
+                if (item >= total) item = -1;
+                else if (b == 0 || !weave) __stcg(A.done + item, mark);
+                else if (atomicExch(A.done + item, mark) == mark) item = -1;  // taken in natural order
             } else {
-                item = k - s_end[kBuckets - 1];
-                if (sched && item < total && __ldcg(A.done + item) == mark) item = -1;  // done from a bucket
-                if (item >= total) item = total;                                      // no work left
+                item = nat;
+                if (item >= total) {
+                    item = total;  // no work left
+                } else if (weave) {
+                    if (atomicExch(A.done + item, mark) == mark) item = -1;  // taken from a bucket
+                } else if (sched && __ldcg(A.done + item) == mark) {
+                    item = -1;  // done from a bucket
+                }
             }
         }
         item = __shfl_sync(kFull, item, 0);
