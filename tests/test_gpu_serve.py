@@ -86,6 +86,47 @@ def test_each_request_same_alone_and_in_the_mix(make_sim, wl):
             assert torch.equal(a, b)
 
 
+def test_served_requests_match_oracle_sampled(make_sim, oracle_mod, wl):
+    """Requests served together (two scenes, 1 to 130 agents, 1 to 5 steps):
+    for two sampled agents of each request the final state matches the FP64
+    oracle's rollout and the last frame matches the oracle's render of that
+    state (depth and colour on unambiguous pixels; misses exact)."""
+    from paper_2407_14783_b300.serve import Server
+    from parity import DEPTH_TOL, DYN_TOL, dyn_error
+    p, sim, scenes, sids = _setup(make_sim, wl)
+    w_h, u_h = _hover(p)
+    specs = [(1, 1, 3), (2, 130, 5), (1, 64, 1), (2, 17, 4), (0, 3, 2), (2, 100, 2)]
+    reqs = []
+    with Server(sim, capacity=512) as srv:
+        tickets = []
+        for k, (si, n, T) in enumerate(specs):
+            s0, cm = _request(wl, scenes[si], n, T, 500 + k, u_h, w_h)
+            out = _outputs(n, T, "last")
+            tickets.append(srv.submit(sids[si], s0, cm, *out, frames="last"))
+            reqs.append((si, s0, cm, out))
+        for t in tickets:
+            srv.wait(t, 60000)
+    rng = np.random.default_rng(3)
+    for si, s0, cm, (st, depth, rgb) in reqs:
+        n = s0.shape[1]
+        pick = rng.choice(n, min(2, n), replace=False)
+        s0_64 = s0.numpy().T[pick].astype(np.float64)
+        u64 = cm.numpy().transpose(0, 2, 1)[:, pick].astype(np.float64)
+        ref = oracle_mod.rollout(p, s0_64, u64)[-1]
+        got = st.numpy().T[pick]
+        assert dyn_error(got, ref)[..., 0:13].max() <= DYN_TOL
+        r = oracle_mod.Scene.from_workload(scenes[si]).render(p, got.astype(np.float64))
+        d, c = depth.numpy()[pick], rgb.numpy()[pick]
+        clear = ~r["tie"]
+        assert r["tie"].mean() < 0.01
+        assert np.array_equal(c[clear], r["rgb"][clear])
+        hitm = clear & (r["id"] >= 0)
+        rel = np.abs(d[hitm].astype(np.float64) - r["depth"][hitm]) / r["depth"][hitm]
+        assert rel.size == 0 or rel.max() <= DEPTH_TOL
+        missm = clear & (r["id"] < 0)
+        assert np.all(d[missm] == np.float32(p["max_depth"])) and np.all(c[missm] == 0)
+
+
 def test_capacity_rejection_and_bad_scene(make_sim, wl):
     from paper_2407_14783_b300.binding import SimError
     from paper_2407_14783_b300.serve import Server
