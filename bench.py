@@ -193,9 +193,10 @@ def cpu_baseline_leg(p, scene, w_h, u_h, budget_s=15.0):
             "tiny_config_agent_frames_per_s": tiny_s}
 
 
-def _recorded_traffic():
-    """DRAM bytes per ray-cast launch from the committed ncu summary, if it was
-    taken on the current kernel source (matching SHA-1), else None."""
+def _recorded_profile():
+    """Figures of one ray-cast launch from the committed ncu summary, if it was
+    taken on the current kernel source (matching SHA-1), else {}: DRAM bytes per
+    launch and the issue-active and ALU-pipe fractions."""
     import hashlib
     src = os.path.join(ROOT, "paper_2407_14783_b300", "csrc", "raycast.cu")
     prof = os.path.join(ROOT, "profiles", "raycast_large_scene_256agents.md")
@@ -205,11 +206,15 @@ def _recorded_traffic():
             if line.startswith("dram_bytes_per_launch"):
                 parts = dict((k.strip(), v.strip()) for k, v in
                              (kv.split("=", 1) for kv in line.split(";") if "=" in kv))
-                if parts.get("raycast_cu_sha1", "").strip() == sha:
-                    return int(parts["dram_bytes_per_launch"].strip())
+                if parts.get("raycast_cu_sha1", "") == sha:
+                    out = {"traffic": int(parts["dram_bytes_per_launch"])}
+                    for k in ("issue_active", "alu_pipe", "l2_throughput", "dram_throughput"):
+                        if k in parts:
+                            out[k] = float(parts[k])
+                    return out
     except Exception:
         pass
-    return None
+    return {}
 
 
 def raycast_roofline(sim, cnt, n, p, render_ms):
@@ -228,7 +233,8 @@ def raycast_roofline(sim, cnt, n, p, render_ms):
     achieved = alg_bytes / (render_ms * 1e-3) / 1e9
     l2 = sim.probe_read_bandwidth(64 << 20, iters=20)
     hbm, hbm_kind = _peaks()
-    traffic = _recorded_traffic()
+    prof = _recorded_profile()
+    traffic = prof.get("traffic")
     hbm_achieved = traffic / (render_ms * 1e-3) / 1e9 if traffic else None
     return {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
             "traffic": traffic, "kernel": "raycast_kernel",
@@ -240,7 +246,11 @@ def raycast_roofline(sim, cnt, n, p, render_ms):
             "per_item": {"rays": rays_per_item, "node_fetches": cnt["node_visits"] / items,
                          "tri_fetches": cnt["tri_tests"] / items, "large_tests": cnt["large_tests"] / items},
             "packet_demand_gbs": (cnt["node_visits"] * 64 + (cnt["tri_tests"] + cnt["large_tests"]) * 48)
-                                 * rays_per_item / (render_ms * 1e-3) / 1e9}
+                                 * rays_per_item / (render_ms * 1e-3) / 1e9,
+            # what limits the kernel in the committed ncu capture of this source:
+            # instruction issue, not L2 or DRAM bandwidth
+            "ncu": {k: prof[k] for k in ("issue_active", "alu_pipe", "l2_throughput", "dram_throughput")
+                    if k in prof} or None}
 
 
 def run_ours(args):
