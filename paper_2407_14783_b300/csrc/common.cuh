@@ -11,7 +11,7 @@ namespace vf {
 constexpr int kStateDim = 17;
 constexpr int kCmdDim = 4;
 constexpr int kMaxSub = 8;      // physics sub-steps per control step
-constexpr int kLeafMax = 4;     // triangles per BVH leaf after collapsing
+constexpr int kLeafMax = 3;     // triangles per BVH leaf after collapsing
 constexpr int kMaxCkptK = 32;   // steps between checkpoints in the rollout adjoint
 constexpr int kEmptyRoot = INT32_MIN;
 

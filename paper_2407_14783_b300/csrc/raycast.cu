@@ -10,7 +10,7 @@
 // broadcast through L1).  Each lane slab-tests both child boxes against its own
 // rays and a warp vote (__ballot_sync) decides which children any ray needs,
 // near child first, the other pushed on the warp's stack (shared memory or a
-// stack spread over the lanes' registers).  Leaves (up to 4 triangles, 12
+// stack spread over the lanes' registers).  Leaves (up to 3 triangles, 9
 // float4, contiguous in leaf order) are fetched the same way and every lane runs
 // Moller-Trumbore on them.  The walk ends when the stack is empty; the votes
 // skip every subtree that no ray of the tile can reach before its current
