@@ -48,7 +48,9 @@ __device__ __forceinline__ void mt_test(Ray& r, const float4 a, const float4 b, 
     const float py = r.d[2] * c.x - r.d[0] * c.z;
     const float pz = r.d[0] * c.y - r.d[1] * c.x;
     const float det = b.x * px + b.y * py + b.z * pz;
-    const float inv = 1.0f / det;
+    // approximate reciprocal (about 1 ulp): t, u, v move by ~1e-7 relative,
+    // far inside the depth tolerance and the 1e-5 edge band of stated ties
+    const float inv = __fdividef(1.0f, det);
     const float sx = r.o[0] - a.x, sy = r.o[1] - a.y, sz = r.o[2] - a.z;
     const float u = (sx * px + sy * py + sz * pz) * inv;
     const float qx = sy * b.z - sz * b.y;
@@ -59,7 +61,7 @@ __device__ __forceinline__ void mt_test(Ray& r, const float4 a, const float4 b, 
     const int id = __float_as_int(a.w);
     const bool hit = det != 0.0f && u >= 0.0f && v >= 0.0f && u + v <= 1.0f && t > kTmin &&
                      (t < r.best_t || (t == r.best_t && (unsigned)id < (unsigned)r.best_id));
-    if (hit && r.live) {
+    if (hit) {
         r.best_t = t;
         r.best_id = id;
     }
@@ -100,7 +102,7 @@ __device__ __forceinline__ bool slab(const Ray& r, float lx, float ly, float lz,
     const float z0 = fmaf(lz, r.inv[2], -r.ood[2]), z1 = fmaf(hz, r.inv[2], -r.ood[2]);
     tn = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), 0.0f));
     const float tf = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), r.best_t));
-    return r.live && tn <= tf;
+    return tn <= tf;  // a dead ray has best_t < 0, so it passes no box
 }
 
 // Fetch `count` (<= 4) consecutive triangle records and test every ray.
@@ -386,7 +388,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                     fhi[j] = fmaxf(fhi[j], e);
                 }
             }
-            ry.best_t = A.cam.max_depth;
+            // a dead ray (outside the image, another quarter, no scene) starts
+            // behind its origin and so passes no box and no triangle test
+            ry.best_t = ry.live ? A.cam.max_depth : -1.0f;
             ry.best_id = -1;
         }
 
@@ -666,7 +670,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                 ((noise_frame * (unsigned long long)A.n_agents + agent) * (unsigned long long)(H * W) +
                  (unsigned long long)(pix_r[q] * W + pix_c[q])) * 64ull;
             if (in && A.depth) {
-                float dv = ray[q].best_t;
+                float dv = ray[q].live ? ray[q].best_t : A.cam.max_depth;
                 if (nz.enabled) dv = noisy(dv, A.cam.max_depth, nz.d_gauss, nz.d_speckle, nz.d_shot, nz.d_sp, nz.seed, nb);
                 A.depth[off] = dv;
             }
