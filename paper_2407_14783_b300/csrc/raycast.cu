@@ -232,7 +232,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
     // mean cost); this launch hands out bucket 0 first, each tile as kSplit
     // quarter-tile sub-packets on separate warps (a quarter walks only its own
     // rays' paths, which shortens the longest dependent chain of node fetches),
-    // then buckets 1-3 whole, then every tile not yet rendered in natural order.
+    // then buckets 1-3 whole, then every tile not yet rendered in natural order
+    // (edge rows first when the buckets hold entries, centre rows first when
+    // they are empty).
     const bool sched = A.sched != nullptr && total <= A.sched_cap;
     // A launch that streams its bands to the host interleaves buckets 1-3 with
     // natural-order items one for one: a band is complete only when all its
@@ -269,6 +271,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
     }
     __syncthreads();
     const float mean = s_mean;
+    const bool hinted = s_end[kBuckets - 1] > 0;
     for (;;) {
         long long item = 0;
         int sub = -1;
@@ -306,7 +309,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                 else if (b == 0 || !weave) __stcg(A.done + item, mark);
                 else if (atomicExch(A.done + item, mark) == mark) item = -1;  // taken in natural order
             } else {
-                item = nat;
+                // with hints, the natural phase holds only tiles the last launch
+                // found cheap; the ones that turn costly lie mostly in the outer
+                // rows (clutter entering the floor or ceiling as a drone
+                // pitches), so those rows go first and the centre rows close
+                // the launch.  Without hints the costly centre rows go first.
+                item = (hinted && !weave && nat < total) ? total - 1 - nat : nat;
                 if (item >= total) {
                     item = total;  // no work left
                 } else if (weave) {
@@ -322,10 +330,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
         if (item >= total) break;
         // after a device-detected fault every warp stops taking work
         if (__shfl_sync(kFull, lane == 0 ? *(volatile int*)A.err : 0, 0) == kDevErrTraversal) break;
-        // Items run tile position by tile position across all agents, tile rows
-        // from the image centre outwards: rows near the horizon (long rays through
-        // clutter) are the costly ones and start first, floor and ceiling rows are
-        // cheap and fill the tail of the launch.
+        // Item ids run tile position by tile position across all agents, tile
+        // rows from the image centre outwards: rows near the horizon (long rays
+        // through clutter) are the costly ones, floor and ceiling rows the cheap
+        // ones.
         const int rank = (int)(item / A.n_agents);
         const int agent = (int)(item - (long long)rank * A.n_agents);
         const int rrow = rank / tiles_x, mid = tiles_y >> 1;

@@ -179,17 +179,18 @@ def test_memory_admission(make_sim, wl):
     _alone(sim0, sids[1], s0, cm, "last")      # the context's render-scheduling hints count too
     base = sim0.mem_usage()[0]
     srv0.close()
-    n, T = 100, 6
+    n, T = 100, 30
     per_req = 4 * (17 * n + T * 4 * n)
     p, sim, scenes, sids = _setup(make_sim, wl, budget=base + int(2.5 * per_req))
     w_h, u_h = _hover(p)
+    # inputs are built first and submitted back to back, so that the budget,
+    # not the time between submissions, decides how many wait in the queue
+    reqs = []
+    for k in range(6):
+        s0, cm = _request(wl, scenes[1], n, T, 200 + k, u_h, w_h)
+        reqs.append((s0, cm, _outputs(n, T, "last")))
     with Server(sim, capacity=512) as srv:
-        reqs, tickets = [], []
-        for k in range(6):
-            s0, cm = _request(wl, scenes[1], n, T, 200 + k, u_h, w_h)
-            out = _outputs(n, T, "last")
-            tickets.append(srv.submit(sids[1], s0, cm, *out))
-            reqs.append((s0, cm, out))
+        tickets = [srv.submit(sids[1], s0, cm, *out) for s0, cm, out in reqs]
         max_queued = 0
         for _ in range(200):
             max_queued = max(max_queued, srv.stats()["queued"])
