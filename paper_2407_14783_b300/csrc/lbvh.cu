@@ -461,7 +461,7 @@ __global__ void pack_colors_kernel(int n, const uint8_t* __restrict__ rgb, uint3
 // surface-area-guided tree needs fewer node visits per ray than the prefix
 // splits.  Node ids come from an exclusive scan over the merging pairs, so the
 // tree does not depend on thread timing.
-constexpr int kPlocRadius = 32;
+constexpr int kPlocRadius = 48;
 constexpr int kPlocBlock = 256;
 constexpr int kPlocMaxDepth = 56;  // deeper trees keep the radix-tree layout (traversal stacks hold 64)
 
