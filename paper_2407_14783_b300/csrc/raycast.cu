@@ -309,11 +309,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                 else if (b == 0 || !weave) __stcg(A.done + item, mark);
                 else if (atomicExch(A.done + item, mark) == mark) item = -1;  // taken in natural order
             } else {
-                // with hints, the natural phase holds only tiles the last launch
-                // found cheap; the ones that turn costly lie mostly in the outer
-                // rows (clutter entering the floor or ceiling as a drone
-                // pitches), so those rows go first and the centre rows close
-                // the launch.  Without hints the costly centre rows go first.
+                // with hints the natural phase holds only tiles the last launch
+                // found cheap, and taking the edge rows first measured faster
+                // (0.8% with moving poses at 4x8 tiles); without hints the
+                // centre rows, where most costly tiles lie, go first
                 item = (hinted && !weave && nat < total) ? total - 1 - nat : nat;
                 if (item >= total) {
                     item = total;  // no work left
