@@ -25,9 +25,22 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+# The current stream's handle without building a torch.cuda.Stream object
+# (3.3 us per call on the B300 host against 0.3 us); falls back to the public
+# call where this torch has no such accessor.
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
+def _stream_handle(stream=None) -> int:
+    if stream is not None:
+        return stream.cuda_stream
+    if _raw_stream is not None:
+        return _raw_stream(torch.cuda.current_device())
+    return torch.cuda.current_stream().cuda_stream
+
+
 def _stream(stream=None):
-    s = stream if stream is not None else torch.cuda.current_stream()
-    return ctypes.c_void_p(s.cuda_stream)
+    return ctypes.c_void_p(_stream_handle(stream))
 
 
 def _need(t, dtype, shape, name):
@@ -296,7 +309,7 @@ class Sim:
                     raise ValueError(f"{('cmd_host', 'depth_host', 'rgb_host', 'state_host')[i]}: "
                                      "need a contiguous host tensor")
                 ptr[i] = t.data_ptr()
-        s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        s = _stream_handle(stream)
         rc = self.L.sim_env_step(self.h, n, scene_of_agent.data_ptr(), state.data_ptr(), ptr[0], ptr[1], ptr[2],
                                  ptr[3], s)
         if rc:
@@ -348,7 +361,7 @@ class Env:
         """One environment step with host commands float32 [4, n]."""
         if cmd_host.is_cuda or not cmd_host.is_contiguous() or cmd_host.numel() != 4 * self.n:
             raise ValueError("cmd_host: need a contiguous host tensor of 4 * n floats")
-        s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        s = _stream_handle(stream)
         rc = self._run(self.h, cmd_host.data_ptr(), s)
         if rc:
             B.check(rc, "sim_env_run", self.sim.h)
