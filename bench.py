@@ -225,6 +225,90 @@ def _recorded_profile():
     return {}
 
 
+# Table II sensor noise at the strengths the sensor parity test uses: depth,
+# colour and segmentation each with Gaussian, speckle, Poisson and
+# salt-and-pepper noise, plus label dropout.
+SENSOR_NOISE = {"seed": 1234, "first_frame": 5, "depth_gauss": 0.02, "depth_speckle": 0.01, "depth_shot": 50.0,
+                "depth_salt_pepper": 0.01, "rgb_gauss": 3.0, "rgb_speckle": 0.02, "rgb_shot": 0.5,
+                "rgb_salt_pepper": 0.01, "seg_dropout": 0.05, "seg_gauss": 0.8, "seg_speckle": 0.01, "seg_shot": 2.0,
+                "seg_salt_pepper": 0.02, "seg_max": 60}
+
+
+def _event_ms(fn, flush, reps):
+    """Mean CUDA-event time of fn() on the current stream, the L2 flushed before each call."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        ts.append((e0, e1))
+    torch.cuda.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in ts)
+
+
+def sensor_extra(sim, scene, sid, ids, state, depth, rgb, flush, n, p, reps=30):
+    """The sensor epilogue (Sec. III-B, Table II): the same renders with a
+    segmentation image, then with every noise model on."""
+    import torch
+    sim.set_labels(sid, np.arange(scene.n_tris, dtype=np.int32) % 60)
+    seg = torch.empty((n, p["height"], p["width"]), dtype=torch.int32, device=state.device)
+    plain = _event_ms(lambda: sim.render(ids, state, depth, rgb), flush, reps)
+    with_seg = _event_ms(lambda: sim.render_seg(ids, state, depth, rgb, None, seg), flush, reps)
+    sim.set_noise(SENSOR_NOISE)
+    noisy = _event_ms(lambda: sim.render_seg(ids, state, depth, rgb, None, seg), flush, reps)
+    sim.set_noise(None)
+    sim.check()
+    return {"agents": n, "render_ms": plain, "with_segmentation_ms": with_seg, "with_segmentation_and_noise_ms": noisy,
+            "agent_frames_per_s_all_sensors": n / (noisy * 1e-3), "pose": "fixed (spawn + one step)"}
+
+
+def controller_extra(sim, p, spawn, n, u_h):
+    """Device time of one control step per controller and integrator setting,
+    20 steps captured in a CUDA graph (no launch gaps)."""
+    import torch
+    dev = spawn.device
+    rng = np.random.default_rng(5)
+    hover = torch.tensor(np.ascontiguousarray(np.broadcast_to([[u_h], [0.0], [0.0], [0.0]], (4, n)), dtype=np.float32),
+                         device=dev)
+    u_srt = 2.0 * p["mass"] * p["g"] / 4 / (p["k"][2] * p["omega_max"] ** 2) - 1.0
+    srt = torch.full((4, n), u_srt, dtype=torch.float32, device=dev)
+    vel = torch.tensor(np.vstack([rng.uniform(-1, 1, (3, n)), np.zeros((1, n))]).astype(np.float32), device=dev)
+    pos = spawn[0:4].clone()
+    pos[0:3] += torch.tensor(rng.uniform(-1.5, 1.5, (3, n)).astype(np.float32), device=dev)
+    pos[3] = 0.0
+    cases = (("ctbr_rk4", {}, hover), ("ctbr_euler", {"integrator": 1}, hover), ("ctbr_rk4_4_substeps", {"n_sub": 4}, hover),
+             ("srt_rk4", {"controller": 1}, srt), ("lv_rk4", {"controller": 2}, vel), ("ps_rk4", {"controller": 3}, pos))
+    out = {}
+    for name, over, cmd in cases:
+        sim.set_params({**p, **over})
+        st = spawn.clone()
+        for _ in range(3):
+            sim.step(st, cmd)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for _ in range(20):
+                sim.step(st, cmd)
+        graph.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) / 20 * 1e3
+        del graph
+        out[name] = {"us_per_step": us, "agent_steps_per_s": n / (us * 1e-6)}
+    sim.set_params(p)
+    sim.check()
+    out["agents"] = n
+    return out
+
+
 def raycast_roofline(sim, cnt, n, p, render_ms):
     """Roofline of the dominant kernel.  Algorithmic bytes per launch (per agent-frame:
     4096 rays x (N_node * 64 B + N_tri * 48 B + 7 B output) + 28 B of pose), with
@@ -408,6 +492,12 @@ def run_ours(args):
     near_ms = e0.elapsed_time(e1) / 20
     del graph
 
+    # the other rows on the path: the sensor epilogue and the other controllers
+    state.copy_(spawn)
+    sim.step(state, cmds[W])
+    sensors = sensor_extra(sim, scene, sid, ids, state, depth, rgb, flush, n, p)
+    controllers = controller_extra(sim, p, spawn, n, u_h)
+
     line = {"metric": METRIC, "value": value, "unit": "agent-frames/s", "n_gpus": ws, "steps": K, "warmup": W,
             "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic (procedural scene, seeded spawns and commands)",
@@ -418,7 +508,8 @@ def run_ours(args):
             "e2e": e2e, "gpu_launches": 2 * K,
             "breakdown_ms": {"dynamics": statistics.mean(dyn_ms), "render": render_ms},
             "roofline": roof,
-            "extras": {"nearest_obstacle": {"agents": n, "ms": near_ms, "queries_per_s": n / (near_ms * 1e-3)}},
+            "extras": {"nearest_obstacle": {"agents": n, "ms": near_ms, "queries_per_s": n / (near_ms * 1e-3)},
+                       "sensors": sensors, "controllers": controllers},
             "clocks": clocks}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg(p, scene, w_h, u_h)
