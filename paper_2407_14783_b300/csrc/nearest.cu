@@ -97,10 +97,12 @@ __device__ __forceinline__ float box_d2(const float p[3], float lx, float ly, fl
 constexpr int kNWarps = 4;       // warps (agents) per block
 constexpr int kNCap = 1024;      // stack entries per warp
 
+// Minimum over the full warp in one instruction (redux.sync on f32, sm_100 and
+// later); exact, so the same as a shuffle ladder.
 __device__ __forceinline__ float warp_min_f(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
+    float r;
+    asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
 }
 
 __global__ void __launch_bounds__(32 * kNWarps) nearest_kernel(NearestArgs A) {

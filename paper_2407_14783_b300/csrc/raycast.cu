@@ -127,15 +127,17 @@ __device__ __forceinline__ void test_leaf(Ray (&ray)[RPL], const float4* __restr
     }
 }
 
+// Minimum / maximum over the full warp in one instruction (sm_100 and later:
+// redux.sync on f32); exact, so the same as a shuffle ladder.
 __device__ __forceinline__ float warp_min(float v) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, off));
-    return v;
+    float r;
+    asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
 }
 __device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, off));
-    return v;
+    float r;
+    asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
 }
 
 // Noise draws of one pixel: 64 consecutive outputs of the generator starting
