@@ -521,6 +521,31 @@ def run_ours(args):
     return 0
 
 
+def multi_scene_cpu_baseline(p, scenes, w_h, u_h, n_pick=8, agents=2, steps=20, seed=77):
+    """Oracle (as it stands) on a bounded sample of a multi-scene workload: two
+    agents in each of eight seeded-random scenes, twenty steps of dynamics and
+    render.  The oracle's own BVH builds are timed apart from the rate."""
+    import oracle
+    oracle.build()
+    pick = sorted(np.random.default_rng(seed).choice(len(scenes), n_pick, replace=False).tolist())
+    frames, t_used, build_s = 0, 0.0, 0.0
+    for i in pick:
+        t0 = time.perf_counter()
+        osc = oracle.Scene.from_workload(scenes[i])
+        build_s += time.perf_counter() - t0
+        s = wl.spawn_states(scenes[i], agents, seed + i, w_h)
+        cmds = wl.hover_commands(steps, agents, seed + 1000 + i, u_h)
+        t0 = time.perf_counter()
+        for t in range(steps):
+            s = oracle.step(p, s, cmds[t])
+            osc.render(p, s)
+        t_used += time.perf_counter() - t0
+        frames += agents * steps
+    return {"value": frames / t_used, "unit": "agent-frames/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{agents} agents x {steps} steps in each of scenes {pick} (dynamics + render, FP64)",
+            "oracle_bvh_build_s": build_s}
+
+
 def batched_scenes(n_scenes=64, lo=10_000, hi=1_000_000, seed=99):
     """64 procedural scenes with log-uniform triangle counts (seeds 100..163)."""
     sizes = wl.Rng(seed).log_uniform(lo, hi, n_scenes)
@@ -599,6 +624,8 @@ def run_batched(args):
                        "scene_generation_s": gen_s, "bvh_build_s": build_s},
             "gpu_launches": args.steps * T * 2,
             "clocks": results["autotuned"]["clk"]}
+    if not getattr(args, "no_cpu_baseline", False):
+        line["cpu_baseline"] = multi_scene_cpu_baseline(p, scenes, w_h, u_h)
     print(json.dumps(line), flush=True)
     sim.close()
     return 0
@@ -861,6 +888,8 @@ def run_serving(args):
                        "triangles_total": int(sum(sc.n_tris for sc in scenes)), "capacity_agents": cap,
                        "seconds_per_load": duration, "scene_generation_s": gen_s},
             "served": levels, "p50_ms": full["p50_ms"], "p99_ms": full["p99_ms"]}
+    if not getattr(args, "no_cpu_baseline", False):
+        line["cpu_baseline"] = multi_scene_cpu_baseline(p, scenes, w_h, u_h)
     print(json.dumps(line), flush=True)
     sim.close()
     return 0
