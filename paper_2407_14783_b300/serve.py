@@ -10,7 +10,6 @@ from __future__ import annotations
 import ctypes
 import threading
 
-import torch
 
 from . import binding as B
 

@@ -1,5 +1,4 @@
 """SRT, LV and PS controllers on the GPU against the oracle (Sec. III-A)."""
-import math
 
 import numpy as np
 import pytest

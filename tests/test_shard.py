@@ -4,7 +4,6 @@ import os
 import socket
 
 import numpy as np
-import pytest
 
 
 def test_plan_covers_every_agent_once_and_balances():

@@ -9,7 +9,6 @@ static device array.  This file is collected last on purpose.
 """
 import ctypes
 
-import numpy as np
 import pytest
 import torch
 
