@@ -287,7 +287,12 @@ int sim_rollout(sim_ctx* ctx, int32_t n_agents, int32_t T, int32_t K, const floa
  * each agent's thread re-runs K steps from a checkpoint, keeps them locally,
  * and walks them backwards.  g_states dev [T+1][17][n] is the cotangent of
  * every state of the trajectory (e.g. dLoss/dstate_t); outputs g_state0 dev
- * [17][n] and g_cmds dev [T][4][n].  K must be 1..32. */
+ * [17][n] and g_cmds dev [T][4][n].  K must be 1..32.
+ * With one sub-step per control step the re-run records each step's forward
+ * pass (264 B per agent and step) in a context-owned buffer of n * K entries,
+ * so the backwards walk does not repeat it.  The buffer is allocated on first
+ * need against the memory budget; where the budget refuses it the walk
+ * recomputes the forward passes instead (same results, slower). */
 int sim_rollout_backward(sim_ctx* ctx, int32_t n_agents, int32_t T, int32_t K, const float* ckpt,
                          const float* cmds, const float* g_states, float* g_state0, float* g_cmds, void* stream);
 

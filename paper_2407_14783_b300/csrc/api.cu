@@ -125,6 +125,9 @@ struct sim_ctx {
     uint8_t* d_rgb = nullptr;
     unsigned* d_band = nullptr;  // completion words of the streamed download
     size_t band_words = 0;
+    // tape of the rollout adjoint's forward passes (sim_rollout_backward)
+    float* d_tape = nullptr;
+    size_t tape_bytes = 0;
     // bumped by every call that changes what a captured environment step
     // launches (parameters, scenes, labels, render config, noise, swarm)
     std::atomic<unsigned long long> generation{1};
@@ -673,6 +676,7 @@ int sim_destroy_ctx(sim_ctx* c) {
     ctx_free(c, c->d_stats, sizeof(long long) * 8);
     ctx_free(c, c->d_noise_frame, sizeof(unsigned long long));
     if (c->sched_mem) ctx_free(c, c->sched_mem, c->sched_bytes);
+    if (c->d_tape) ctx_free(c, c->d_tape, c->tape_bytes);
     ctx_free(c, c->d_cmd, 0);
     ctx_free(c, c->d_depth, 0);
     ctx_free(c, c->d_rgb, 0);
@@ -844,8 +848,30 @@ int sim_rollout_backward(sim_ctx* c, int32_t n, int32_t T, int32_t K, const floa
         return fail(SIM_ERR_INVALID_ARG, "bad sim_rollout_backward arguments");
     if (c->dyn.controller > 1) return fail(SIM_ERR_INVALID_ARG, "the adjoint covers the CTBR and SRT controllers");
     DeviceGuard g(c->device);
-    cudaError_t e =
-        launch_rollout_backward(c->dyn, n, T, K, ckpt, cmds, g_states, g_state0, g_cmds, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    // With one sub-step per control step the adjoint records each step's
+    // forward pass instead of running it twice; the tape is grown on demand
+    // and, where the memory budget refuses it, the sweep recomputes instead.
+    float* tape = nullptr;
+    if (c->dyn.n_sub == 1 && n > 0) {
+        const size_t need = rollout_tape_bytes(n, K);
+        if (need > c->tape_bytes) {
+            cudaStreamSynchronize(s);
+            if (c->d_tape) ctx_free(c, c->d_tape, c->tape_bytes);
+            c->d_tape = nullptr;
+            c->tape_bytes = 0;
+            void* p = nullptr;
+            const std::string before = g_err;
+            if (ctx_alloc(c, need, &p) == SIM_OK) {
+                c->d_tape = (float*)p;
+                c->tape_bytes = need;
+            } else {
+                g_err = before;  // not an error of this call: it recomputes instead
+            }
+        }
+        tape = c->d_tape;
+    }
+    cudaError_t e = launch_rollout_backward(c->dyn, n, T, K, ckpt, cmds, g_states, g_state0, g_cmds, tape, s);
     return e == cudaSuccess ? SIM_OK : cuda_fail(e, "sim_rollout_backward launch");
 }
 

@@ -443,51 +443,124 @@ __device__ void rhs_vjp(const DynConsts& c, const float y[13], float Fz, const f
 
 // Reverse mode of one sub-step: y_in (pre), u, cotangent gout of the post-sub-
 // step state -> gin (cotangent of y_in) and accumulated gu.
-__device__ void substep_vjp(const DynConsts& c, const float y_in[17], const float u[4], const float gout[17],
-                            float gin[17], float gu[4]) {
-    // forward recompute
+// What the reverse sweep of one sub-step needs from its forward pass: the
+// controller's tape, the held collective thrust, the lagged rotor speeds, the
+// inputs of RK4 stages 2-4 (stage 1 starts from the sub-step's own input) and
+// the un-normalised result.
+struct StepTape {
+    CtrlTape ctrl;
+    float Fz, w[4];
+    float ys[3][13];
+    float yn[13];
+};
+constexpr int kTapeWords = 4 + 4 + 1 + 1 + 4 + 3 * 13 + 13;  // fc, dw_df, flag bits, Fz, w, ys, yn
+
+// Forward pass of one sub-step from y_in, recording the tape (the same
+// arithmetic as substep()).
+__device__ void substep_record(const DynConsts& c, const float y_in[17], const float u[4], StepTape& T) {
     float y[17];
 #pragma unroll
     for (int j = 0; j < 17; ++j) y[j] = y_in[j];
-    CtrlTape tape;
-    float Fz, eta[3];
-    rotors(c, y, u, Fz, eta, &tape);
+    float eta[3];
+    rotors(c, y, u, T.Fz, eta, &T.ctrl);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) T.w[i] = y[13 + i];
     const float h = c.h;
-    float ys[4][13];
-    float yn[13];
     if (c.integrator == 1) {
         float k1[13];
+        rhs(c, y, T.Fz, eta, k1);
 #pragma unroll
-        for (int j = 0; j < 13; ++j) ys[0][j] = y[j];
-        rhs(c, ys[0], Fz, eta, k1);
-#pragma unroll
-        for (int j = 0; j < 13; ++j) yn[j] = ys[0][j] + h * k1[j];
+        for (int j = 0; j < 13; ++j) T.yn[j] = y[j] + h * k1[j];
     } else {
         float k[13], acc[13];
-#pragma unroll
-        for (int j = 0; j < 13; ++j) ys[0][j] = y[j];
-        rhs(c, ys[0], Fz, eta, k);
+        rhs(c, y, T.Fz, eta, k);
 #pragma unroll
         for (int j = 0; j < 13; ++j) {
             acc[j] = k[j];
-            ys[1][j] = y[j] + 0.5f * h * k[j];
+            T.ys[0][j] = y[j] + 0.5f * h * k[j];
         }
-        rhs(c, ys[1], Fz, eta, k);
+        rhs(c, T.ys[0], T.Fz, eta, k);
 #pragma unroll
         for (int j = 0; j < 13; ++j) {
             acc[j] += 2.0f * k[j];
-            ys[2][j] = y[j] + 0.5f * h * k[j];
+            T.ys[1][j] = y[j] + 0.5f * h * k[j];
         }
-        rhs(c, ys[2], Fz, eta, k);
+        rhs(c, T.ys[1], T.Fz, eta, k);
 #pragma unroll
         for (int j = 0; j < 13; ++j) {
             acc[j] += 2.0f * k[j];
-            ys[3][j] = y[j] + h * k[j];
+            T.ys[2][j] = y[j] + h * k[j];
         }
-        rhs(c, ys[3], Fz, eta, k);
+        rhs(c, T.ys[2], T.Fz, eta, k);
 #pragma unroll
-        for (int j = 0; j < 13; ++j) yn[j] = y[j] + (h / 6.0f) * (acc[j] + k[j]);
+        for (int j = 0; j < 13; ++j) T.yn[j] = y[j] + (h / 6.0f) * (acc[j] + k[j]);
     }
+}
+
+// A tape as kTapeWords columns of n agents (word f of agent a at f * n + a),
+// so that a warp's stores and loads of one word are coalesced.
+__device__ void tape_store(const StepTape& T, float* __restrict__ base, int n, int a) {
+    unsigned bits = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        base[(size_t)i * n + a] = T.ctrl.fc[i];
+        base[(size_t)(4 + i) * n + a] = T.ctrl.dw_df[i];
+        bits |= (T.ctrl.in_f[i] ? 1u : 0u) << i;
+        bits |= (T.ctrl.in_w[i] ? 1u : 0u) << (4 + i);
+    }
+    base[(size_t)8 * n + a] = __uint_as_float(bits);
+    base[(size_t)9 * n + a] = T.Fz;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) base[(size_t)(10 + i) * n + a] = T.w[i];
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+#pragma unroll
+        for (int j = 0; j < 13; ++j) base[(size_t)(14 + 13 * s + j) * n + a] = T.ys[s][j];
+#pragma unroll
+    for (int j = 0; j < 13; ++j) base[(size_t)(53 + j) * n + a] = T.yn[j];
+}
+__device__ void tape_load(StepTape& T, const float* __restrict__ base, int n, int a) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        T.ctrl.fc[i] = base[(size_t)i * n + a];
+        T.ctrl.dw_df[i] = base[(size_t)(4 + i) * n + a];
+    }
+    const unsigned bits = __float_as_uint(base[(size_t)8 * n + a]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        T.ctrl.in_f[i] = (bits >> i) & 1u;
+        T.ctrl.in_w[i] = (bits >> (4 + i)) & 1u;
+    }
+    T.Fz = base[(size_t)9 * n + a];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) T.w[i] = base[(size_t)(10 + i) * n + a];
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+#pragma unroll
+        for (int j = 0; j < 13; ++j) T.ys[s][j] = base[(size_t)(14 + 13 * s + j) * n + a];
+#pragma unroll
+    for (int j = 0; j < 13; ++j) T.yn[j] = base[(size_t)(53 + j) * n + a];
+}
+
+// The state after the recorded sub-step, exactly as substep() leaves it.
+__device__ __forceinline__ void substep_result(const StepTape& T, float y[17]) {
+#pragma unroll
+    for (int j = 0; j < 13; ++j) y[j] = T.yn[j];
+    const float qn = rsqrtf(y[6] * y[6] + y[7] * y[7] + y[8] * y[8] + y[9] * y[9]);
+#pragma unroll
+    for (int j = 6; j < 10; ++j) y[j] *= qn;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) y[13 + i] = T.w[i];
+}
+
+// Reverse sweep of one sub-step from its recorded forward pass.
+__device__ void substep_reverse(const DynConsts& c, const float y_in[17], const float u[4], const StepTape& T,
+                                const float gout[17], float gin[17], float gu[4]) {
+    const CtrlTape& tape = T.ctrl;
+    const float Fz = T.Fz;
+    const float h = c.h;
+    const float* ys[4] = {y_in, T.ys[0], T.ys[1], T.ys[2]};
+    const float (&yn)[13] = T.yn;
     // normalisation q <- q / |q|
     float ybn[13];
 #pragma unroll
@@ -556,7 +629,7 @@ __device__ void substep_vjp(const DynConsts& c, const float y_in[17], const floa
     float fb[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const float w = y[13 + i];  // lagged rotor speed
+        const float w = T.w[i];  // lagged rotor speed
         const float fbi = Fzb + c.mix[0][i] * etab[0] + c.mix[1][i] * etab[1] + c.mix[2][i] * etab[2];
         const float wb = gout[13 + i] + fbi * (2.0f * c.k2 * w + c.k1);
         gin[13 + i] = wb * c.decay;
@@ -589,6 +662,14 @@ __device__ void substep_vjp(const DynConsts& c, const float y_in[17], const floa
     }
 #pragma unroll
     for (int j = 0; j < 13; ++j) gin[j] = yb[j];
+}
+
+// Reverse mode of one sub-step: its forward pass, then its reverse sweep.
+__device__ void substep_vjp(const DynConsts& c, const float y_in[17], const float u[4], const float gout[17],
+                            float gin[17], float gu[4]) {
+    StepTape T;
+    substep_record(c, y_in, u, T);
+    substep_reverse(c, y_in, u, T, gout, gin, gu);
 }
 
 // Reverse mode of a full control step (n_sub sub-steps): the sub-step start
@@ -688,10 +769,14 @@ __global__ void __launch_bounds__(64) rollout_backward_kernel(DynConsts c, int n
                                                               const float* __restrict__ cmds,
                                                               const float* __restrict__ g_states,
                                                               float* __restrict__ g_state0,
-                                                              float* __restrict__ g_cmds) {
+                                                              float* __restrict__ g_cmds, float* __restrict__ tape) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= n) return;
     float seg[kMaxCkptK][17];
+    // with one sub-step per control step, and tape memory given, the
+    // segment's forward passes are recorded while the segment is recomputed,
+    // so the reverse sweep does not run them a second time
+    const bool taped = tape != nullptr && c.n_sub == 1;
     float g[17];
     load_state(g_states + (size_t)T * 17 * n, n, a, g);
     const int nseg = (T + K - 1) / K;
@@ -699,17 +784,30 @@ __global__ void __launch_bounds__(64) rollout_backward_kernel(DynConsts c, int n
         const int t0 = s * K;
         const int t1 = min(t0 + K, T);
         load_state(ckpt + (size_t)s * 17 * n, n, a, seg[0]);
-        for (int t = t0 + 1; t < t1; ++t) {
+        for (int t = t0 + 1; t < (taped ? t1 + 1 : t1); ++t) {
             float u[4];
-#pragma unroll
-            for (int j = 0; j < 17; ++j) seg[t - t0][j] = seg[t - t0 - 1][j];
             load_cmd(cmds + (size_t)(t - 1) * 4 * n, n, a, u);
-            control_step(c, seg[t - t0], u);
+            if (taped) {
+                StepTape rec;
+                substep_record(c, seg[t - 1 - t0], u, rec);
+                tape_store(rec, tape + (size_t)(t - 1 - t0) * kTapeWords * n, n, a);
+                if (t < t1) substep_result(rec, seg[t - t0]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 17; ++j) seg[t - t0][j] = seg[t - t0 - 1][j];
+                control_step(c, seg[t - t0], u);
+            }
         }
         for (int t = t1 - 1; t >= t0; --t) {
             float u[4], gi[17], gu[4] = {0.0f, 0.0f, 0.0f, 0.0f};
             load_cmd(cmds + (size_t)t * 4 * n, n, a, u);
-            control_step_vjp(c, seg[t - t0], u, g, gi, gu);
+            if (taped) {
+                StepTape rec;
+                tape_load(rec, tape + (size_t)(t - t0) * kTapeWords * n, n, a);
+                substep_reverse(c, seg[t - t0], u, rec, g, gi, gu);
+            } else {
+                control_step_vjp(c, seg[t - t0], u, g, gi, gu);
+            }
 #pragma unroll
             for (int j = 0; j < 4; ++j) g_cmds[((size_t)t * 4 + j) * n + a] = gu[j];
             float gs[17];
@@ -745,10 +843,14 @@ cudaError_t launch_rollout(const DynConsts& c, int n, int T, int K, const float*
     return cudaGetLastError();
 }
 
+size_t rollout_tape_bytes(int n, int K) { return sizeof(float) * kTapeWords * (size_t)K * (size_t)n; }
+
 cudaError_t launch_rollout_backward(const DynConsts& c, int n, int T, int K, const float* ckpt, const float* cmds,
-                                    const float* g_states, float* g_state0, float* g_cmds, cudaStream_t s) {
+                                    const float* g_states, float* g_state0, float* g_cmds, float* tape,
+                                    cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    rollout_backward_kernel<<<blocks_for(n, 64), 64, 0, s>>>(c, n, T, K, ckpt, cmds, g_states, g_state0, g_cmds);
+    rollout_backward_kernel<<<blocks_for(n, 64), 64, 0, s>>>(c, n, T, K, ckpt, cmds, g_states, g_state0, g_cmds,
+                                                             tape);
     return cudaGetLastError();
 }
 

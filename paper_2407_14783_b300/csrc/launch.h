@@ -16,8 +16,12 @@ cudaError_t launch_step_backward(const DynConsts& c, int n, const float* state_i
                                  const float* g_out, float* g_in, float* g_cmd, cudaStream_t s);
 cudaError_t launch_rollout(const DynConsts& c, int n, int T, int K, const float* state0, const float* cmds,
                            float* states_out, float* ckpt, float* state_final, cudaStream_t s);
+// tape: scratch of rollout_tape_bytes(n, K) bytes that records each step's
+// forward pass for the reverse sweep, or null (the sweep then recomputes it)
 cudaError_t launch_rollout_backward(const DynConsts& c, int n, int T, int K, const float* ckpt, const float* cmds,
-                                    const float* g_states, float* g_state0, float* g_cmds, cudaStream_t s);
+                                    const float* g_states, float* g_state0, float* g_cmds, float* tape,
+                                    cudaStream_t s);
+size_t rollout_tape_bytes(int n, int K);
 
 // lbvh.cu
 struct LbvhResult {
