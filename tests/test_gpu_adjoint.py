@@ -73,6 +73,38 @@ def test_rollout_gradient_matches_oracle(make_sim, oracle_mod, wl, T, K):
         assert _rel(full, ref) < GRAD_TOL, (a, _rel(full, ref))
 
 
+def test_rollout_adjoint_without_tape_memory(make_sim, oracle_mod, wl):
+    """Under a memory budget too small for the adjoint's tape of forward passes,
+    the sweep recomputes them instead: no memory is taken, no error is left
+    behind, and the gradients match the taped run's and the FP64 oracle's."""
+    p = wl.params()
+    w_h, u_h = _hover(p)
+    sc = wl.room_scene()
+    n, T, K = 32, 20, 5
+    s0 = wl.spawn_states(sc, n, 71, w_h).astype(np.float32)
+    U = wl.hover_commands(T, n, 72, u_h).astype(np.float32)
+    goals = wl.goal_points(sc, n, 73).astype(np.float32)
+    lam = 0.01
+    taped = make_sim(p)
+    L1, gs1, gu1 = _loss_and_grads(taped, s0, U, goals, lam, K)
+    probe = make_sim(p)
+    base = probe.mem_usage()[0]
+    tight = make_sim(p, mem_budget=base + 1024)        # room for nothing more
+    L2, gs2, gu2 = _loss_and_grads(tight, s0, U, goals, lam, K)
+    assert tight.mem_usage()[0] == base
+    assert taped.mem_usage()[0] > base                 # the unconstrained run did keep a tape
+    tight.check()
+    assert np.allclose(L1, L2, rtol=1e-6)
+    Lr, gsr, gur = oracle_mod.rollout_loss_grad(p, s0.astype(np.float64), U.astype(np.float64),
+                                                goals.astype(np.float64), lam)
+    for a in range(n):
+        g1 = np.concatenate([gs1[a], gu1[:, a].ravel()])
+        g2 = np.concatenate([gs2[a], gu2[:, a].ravel()])
+        ref = np.concatenate([gsr[a], gur[:, a].ravel()])
+        assert _rel(g2, g1) < 1e-4, (a, _rel(g2, g1))
+        assert _rel(g2, ref) < GRAD_TOL, (a, _rel(g2, ref))
+
+
 def test_rollout_gradient_long_horizon_sampled(make_sim, oracle_mod, wl):
     """Differentiable-rollout configuration: 1,024 agents, 200 steps, checkpoints
     every 10 steps; 6 sampled agents checked against the exact FP64 gradient."""
