@@ -260,10 +260,14 @@ def sensor_extra(sim, scene, sid, ids, state, depth, rgb, flush, n, p, reps=30):
     with_seg = _event_ms(lambda: sim.render_seg(ids, state, depth, rgb, None, seg), flush, reps)
     sim.set_noise(SENSOR_NOISE)
     noisy = _event_ms(lambda: sim.render_seg(ids, state, depth, rgb, None, seg), flush, reps)
+    # a lighter setting: additive Gaussian noise on depth and colour only
+    sim.set_noise({"seed": 1234, "depth_gauss": 0.02, "rgb_gauss": 3.0})
+    gauss = _event_ms(lambda: sim.render(ids, state, depth, rgb), flush, reps)
     sim.set_noise(None)
     sim.check()
     return {"agents": n, "render_ms": plain, "with_segmentation_ms": with_seg, "with_segmentation_and_noise_ms": noisy,
-            "agent_frames_per_s_all_sensors": n / (noisy * 1e-3), "pose": "fixed (spawn + one step)"}
+            "with_depth_and_rgb_gauss_ms": gauss, "agent_frames_per_s_all_sensors": n / (noisy * 1e-3),
+            "pose": "fixed (spawn + one step)"}
 
 
 def controller_extra(sim, p, spawn, n, u_h):
