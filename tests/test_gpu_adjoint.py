@@ -73,6 +73,34 @@ def test_rollout_gradient_matches_oracle(make_sim, oracle_mod, wl, T, K):
         assert _rel(full, ref) < GRAD_TOL, (a, _rel(full, ref))
 
 
+@pytest.mark.parametrize("over", [{"integrator": 1}, {"controller": 1}, {"n_sub": 2}])
+def test_rollout_gradient_variants_match_oracle(make_sim, oracle_mod, wl, over):
+    """The rollout adjoint with the Euler integrator and the SRT controller (both
+    through the recorded forward passes) and with two sub-steps per control step
+    (re-run forward passes), against the exact FP64 gradient."""
+    p = wl.params(**over)
+    w_h, u_h = _hover(p)
+    sc = wl.room_scene()
+    n, T, K = 16, 12, 4
+    s0 = wl.spawn_states(sc, n, 81, w_h).astype(np.float32)
+    if over.get("controller") == 1:
+        u_srt = 2.0 * p["mass"] * p["g"] / 4 / (p["k"][2] * p["omega_max"] ** 2) - 1.0
+        U = (u_srt + wl.Rng(82).uniform(-0.02, 0.02, (T, n, 4))).astype(np.float32)
+    else:
+        U = wl.hover_commands(T, n, 82, u_h).astype(np.float32)
+    goals = wl.goal_points(sc, n, 83).astype(np.float32)
+    lam = 0.01
+    sim = make_sim(p)
+    L, gs, gu = _loss_and_grads(sim, s0, U, goals, lam, K)
+    Lr, gsr, gur = oracle_mod.rollout_loss_grad(p, s0.astype(np.float64), U.astype(np.float64),
+                                                goals.astype(np.float64), lam)
+    assert np.allclose(L, Lr, rtol=1e-4)
+    for a in range(n):
+        full = np.concatenate([gs[a], gu[:, a].ravel()])
+        ref = np.concatenate([gsr[a], gur[:, a].ravel()])
+        assert _rel(full, ref) < GRAD_TOL, (a, _rel(full, ref))
+
+
 def test_rollout_adjoint_without_tape_memory(make_sim, oracle_mod, wl):
     """Under a memory budget too small for the adjoint's tape of forward passes,
     the sweep recomputes them instead: no memory is taken, no error is left
