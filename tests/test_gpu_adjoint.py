@@ -101,6 +101,29 @@ def test_rollout_gradient_variants_match_oracle(make_sim, oracle_mod, wl, over):
         assert _rel(full, ref) < GRAD_TOL, (a, _rel(full, ref))
 
 
+def test_rollout_adjoint_tape_grows(make_sim, wl):
+    """A context whose tape was sized for a small rollout grows it for a larger
+    one (more agents, longer segments) and gives exactly the gradients of a
+    fresh context."""
+    p = wl.params()
+    w_h, u_h = _hover(p)
+    sc = wl.room_scene()
+    small = make_sim(p)
+    s0 = wl.spawn_states(sc, 8, 91, w_h).astype(np.float32)
+    U = wl.hover_commands(8, 8, 92, u_h).astype(np.float32)
+    goals = wl.goal_points(sc, 8, 93).astype(np.float32)
+    _loss_and_grads(small, s0, U, goals, 0.01, 4)
+    used = small.mem_usage()[0]
+    n, T, K = 48, 24, 8
+    s0 = wl.spawn_states(sc, n, 94, w_h).astype(np.float32)
+    U = wl.hover_commands(T, n, 95, u_h).astype(np.float32)
+    goals = wl.goal_points(sc, n, 96).astype(np.float32)
+    L1, gs1, gu1 = _loss_and_grads(small, s0, U, goals, 0.01, K)
+    assert small.mem_usage()[0] > used
+    L2, gs2, gu2 = _loss_and_grads(make_sim(p), s0, U, goals, 0.01, K)
+    assert np.array_equal(L1, L2) and np.array_equal(gs1, gs2) and np.array_equal(gu1, gu2)
+
+
 def test_rollout_adjoint_without_tape_memory(make_sim, oracle_mod, wl):
     """Under a memory budget too small for the adjoint's tape of forward passes,
     the sweep recomputes them instead: no memory is taken, no error is left
