@@ -281,6 +281,13 @@ int derive(const sim_params& p, DynConsts& d, CamConsts& cam) {
     d.xk1sq = pair(d.dk[1] * d.dk[1]);
     d.x4k2 = pair(4.0 * d.dk[2]);
     d.xhalf_f_hi = pair(0.5 * d.df_hi);
+    for (int j = 0; j < 3; ++j) {
+        d.xmKpos[j] = pair(d.dmass * d.dKpos[j]);
+        d.xmKvel[j] = pair(d.dmass * d.dKvel[j]);
+        d.xJKatt[j] = pair(d.dJ[j] * d.dKatt[j]);
+        d.xJKom[j] = pair(d.dJ[j] * d.dKom[j]);
+    }
+    d.xmg = pair(d.dmass * d.dg);
     d.omega_min = p.omega_min;
     d.omega_max = p.omega_max;
     const double h = (double)p.dt / p.n_sub;

@@ -47,9 +47,6 @@ struct CtrlTape {
     bool in_w[4];     // rotor speed inside [omega_min, omega_max]
 };
 
-// Thrust allocation shared by the controllers, in FP64: rotor thrusts
-// f = Ainv (collective thrust, moment), clamped to the reachable range, and
-// the desired rotor speeds from the thrust polynomial's positive root.
 // ---------------------------------------------------------------- double-float
 // A value as the unevaluated sum hi + lo of two floats (about 48 significant
 // bits), built from exact products (FMA) and exact sums (Knuth's two-sum).
@@ -85,6 +82,38 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
 }
 __device__ __forceinline__ bool df_lt(dfl a, dfl b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 __device__ __forceinline__ float df_float(dfl a) { return __fadd_rn(a.hi, a.lo); }
+__device__ __forceinline__ dfl df_twice(dfl a) { return {__fmul_rn(2.0f, a.hi), __fmul_rn(2.0f, a.lo)}; }
+// a / b: an FP32 quotient, then one correction from the double-float
+// remainder a - q b (relative error about 1e-14).
+__device__ __forceinline__ dfl df_div(dfl a, dfl b) {
+    const float r = __frcp_rn(b.hi);
+    const float q = __fmul_rn(a.hi, r);
+    const dfl rem = df_sub(a, df_mul(b, df_of(q)));
+    return df_norm(q, __fmul_rn(rem.hi, r));
+}
+// sqrt(a) for a >= 0: the FP32 root s, then one Newton correction
+// (a - s^2) / (2 s) with s^2 formed exactly.
+__device__ __forceinline__ dfl df_sqrt(dfl a) {
+    const float s = __fsqrt_rn(a.hi);
+    if (!(s > 0.0f)) return {s, 0.0f};
+    const float p = __fmul_rn(s, s);
+    const dfl rem = df_sub(a, dfl{p, __fmaf_rn(s, s, -p)});
+    return df_norm(s, __fmul_rn(rem.hi, __frcp_rn(__fmul_rn(2.0f, s))));
+}
+__device__ __forceinline__ dfl df_dot3(const dfl a[3], const dfl b[3]) {
+    return df_add(df_add(df_mul(a[0], b[0]), df_mul(a[1], b[1])), df_mul(a[2], b[2]));
+}
+// a x b
+__device__ __forceinline__ void df_cross(const dfl a[3], const dfl b[3], dfl r[3]) {
+    r[0] = df_sub(df_mul(a[1], b[2]), df_mul(a[2], b[1]));
+    r[1] = df_sub(df_mul(a[2], b[0]), df_mul(a[0], b[2]));
+    r[2] = df_sub(df_mul(a[0], b[1]), df_mul(a[1], b[0]));
+}
+
+// ---------------------------------------------------------------- thrust allocation
+// Shared by the controllers: rotor thrusts f = Ainv (collective thrust,
+// moment), clamped to the reachable range, and the desired rotor speeds from
+// the thrust polynomial's positive root.
 
 // Rotor speed of thrust fc, the positive root of k2 w^2 + k1 w + k0 = fc
 // (Eq. 4 inverted); dw = dw/dfc.  The discriminant k1^2 - 4 k2 (k0 - fc) is a
@@ -133,12 +162,6 @@ __device__ __forceinline__ void allocate(const DynConsts& c, const dfl rhs[4], f
     }
 }
 
-__device__ __forceinline__ void dcross(const double a[3], const double b[3], double r[3]) {
-    r[0] = a[1] * b[2] - a[2] * b[1];
-    r[1] = a[2] * b[0] - a[0] * b[2];
-    r[2] = a[0] * b[1] - a[1] * b[0];
-}
-
 // CTBR: u0 -> collective thrust m a, u1..3 -> desired rates; P rate loop with
 // gyroscopic feed-forward -> desired moment (Sec. III-A; the action type of the
 // paper's examples, Sec. IV).
@@ -163,80 +186,85 @@ __device__ __forceinline__ void ctbr_rhs(const DynConsts& c, const float Om[3], 
 // collective thrust = its projection on body z; desired attitude from the
 // force direction and the yaw command; moment from the attitude and rate
 // errors plus the gyroscopic term.  u = (target, yaw) in m or m/s and rad.
-__device__ void geometric_rhs(const DynConsts& c, const float y[17], const float u[4], bool position,
-                              double rhs[4]) {
-    const double q[4] = {y[6], y[7], y[8], y[9]};
-    const double inv_n = 1.0 / (q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-    const double w = q[0], x = q[1], yy = q[2], z = q[3];
-    double R[3][3];
-    R[0][0] = (w * w + x * x - yy * yy - z * z) * inv_n;
-    R[0][1] = 2.0 * (x * yy - w * z) * inv_n;
-    R[0][2] = 2.0 * (x * z + w * yy) * inv_n;
-    R[1][0] = 2.0 * (x * yy + w * z) * inv_n;
-    R[1][1] = (w * w - x * x + yy * yy - z * z) * inv_n;
-    R[1][2] = 2.0 * (yy * z - w * x) * inv_n;
-    R[2][0] = 2.0 * (x * z - w * yy) * inv_n;
-    R[2][1] = 2.0 * (yy * z + w * x) * inv_n;
-    R[2][2] = (w * w - x * x - yy * yy + z * z) * inv_n;
-    double F[3];
+// On double-float pairs like the CTBR law; only the yaw's sine and cosine are
+// taken in FP64.  R is used unnormalised (Rr = |q|^2 R): the collective thrust
+// and the attitude error are linear in it and take the 1/|q|^2 at the end.
+__device__ void geometric_rhs(const DynConsts& c, const float y[17], const float u[4], bool position, dfl rhs[4]) {
+    double sy_d, cy_d;
+    sincos((double)u[3], &sy_d, &cy_d);
+    const float w = y[6], x = y[7], yq = y[8], z = y[9];
+    auto pr = [](float a, float b) { return df_mul(df_of(a), df_of(b)); };  // exact
+    const dfl ww = pr(w, w), xx = pr(x, x), yy = pr(yq, yq), zz = pr(z, z);
+    const dfl xy = pr(x, yq), wz = pr(w, z), xz = pr(x, z), wy = pr(w, yq), yz = pr(yq, z), wx = pr(w, x);
+    const dfl inv_n = df_div(df_of(1.0f), df_add(df_add(ww, xx), df_add(yy, zz)));
+    dfl Rr[3][3];
+    Rr[0][0] = df_sub(df_add(ww, xx), df_add(yy, zz));
+    Rr[0][1] = df_twice(df_sub(xy, wz));
+    Rr[0][2] = df_twice(df_add(xz, wy));
+    Rr[1][0] = df_twice(df_add(xy, wz));
+    Rr[1][1] = df_sub(df_add(ww, yy), df_add(xx, zz));
+    Rr[1][2] = df_twice(df_sub(yz, wx));
+    Rr[2][0] = df_twice(df_sub(xz, wy));
+    Rr[2][1] = df_twice(df_add(yz, wx));
+    Rr[2][2] = df_sub(df_add(ww, zz), df_add(xx, yy));
+    dfl F[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const double acc = position ? (-c.dKpos[j] * ((double)y[j] - (double)u[j]) - c.dKvel[j] * (double)y[3 + j])
-                                    : (-c.dKvel[j] * ((double)y[3 + j] - (double)u[j]));
-        F[j] = c.dmass * acc;
+        if (position)
+            F[j] = df_neg(df_add(df_mul(df_of(c.xmKpos[j]), df_two_sum(y[j], -u[j])),
+                                 df_mul(df_of(c.xmKvel[j]), df_of(y[3 + j]))));
+        else
+            F[j] = df_neg(df_mul(df_of(c.xmKvel[j]), df_two_sum(y[3 + j], -u[j])));
     }
-    F[2] += c.dmass * c.dg;
-    const double f_coll = F[0] * R[0][2] + F[1] * R[1][2] + F[2] * R[2][2];
-    const double nF = sqrt(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
-    double b3[3] = {0.0, 0.0, 1.0};
-    if (nF >= 1e-9) {
-        b3[0] = F[0] / nF;
-        b3[1] = F[1] / nF;
-        b3[2] = F[2] / nF;
+    F[2] = df_add(F[2], df_of(c.xmg));
+    const dfl col2[3] = {Rr[0][2], Rr[1][2], Rr[2][2]};
+    rhs[0] = df_mul(df_dot3(F, col2), inv_n);
+    dfl b3[3] = {df_of(0.0f), df_of(0.0f), df_of(1.0f)};
+    const dfl nF = df_sqrt(df_dot3(F, F));
+    if (nF.hi >= 1e-9f) {
+        const dfl r = df_div(df_of(1.0f), nF);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) b3[k] = df_mul(F[k], r);
     }
-    double sy, cy;
-    sincos((double)u[3], &sy, &cy);
-    double c1[3] = {cy, sy, 0.0}, b2[3];
-    dcross(b3, c1, b2);
-    double n2 = sqrt(b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]);
-    if (n2 < 1e-6) {
-        const double c1b[3] = {-sy, cy, 0.0};
-        dcross(b3, c1b, b2);
-        n2 = sqrt(b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]);
+    const float sy_hi = (float)sy_d, cy_hi = (float)cy_d;
+    const dfl sy = {sy_hi, (float)(sy_d - (double)sy_hi)}, cy = {cy_hi, (float)(cy_d - (double)cy_hi)};
+    const dfl zero = df_of(0.0f);
+    const dfl c1[3] = {cy, sy, zero};
+    dfl b2[3];
+    df_cross(b3, c1, b2);
+    dfl n2 = df_sqrt(df_dot3(b2, b2));
+    if (n2.hi < 1e-6f) {
+        const dfl c1b[3] = {df_neg(sy), cy, zero};
+        df_cross(b3, c1b, b2);
+        n2 = df_sqrt(df_dot3(b2, b2));
     }
-    b2[0] /= n2;
-    b2[1] /= n2;
-    b2[2] /= n2;
-    double b1[3];
-    dcross(b2, b3, b1);
-    double Rd[3][3];
+    const dfl r2 = df_div(df_of(1.0f), n2);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        Rd[i][0] = b1[i];
-        Rd[i][1] = b2[i];
-        Rd[i][2] = b3[i];
+    for (int k = 0; k < 3; ++k) b2[k] = df_mul(b2[k], r2);
+    dfl b1[3];
+    df_cross(b2, b3, b1);
+    // vee of M = Rd^T R - R^T Rd with Rd = [b1 b2 b3]: the entries (2,1),
+    // (0,2), (1,0), i.e. sum_k Rd[k][i] R[k][j] - R[k][i] Rd[k][j]
+    const dfl* bcol[3] = {b1, b2, b3};
+    const int I[3] = {2, 0, 1}, J[3] = {1, 2, 0};
+    dfl eR[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int i = I[e], j = J[e];
+        dfl m = df_sub(df_mul(bcol[i][0], Rr[0][j]), df_mul(Rr[0][i], bcol[j][0]));
+#pragma unroll
+        for (int k = 1; k < 3; ++k)
+            m = df_add(m, df_sub(df_mul(bcol[i][k], Rr[k][j]), df_mul(Rr[k][i], bcol[j][k])));
+        const dfl mn = df_mul(m, inv_n);
+        eR[e] = {__fmul_rn(0.5f, mn.hi), __fmul_rn(0.5f, mn.lo)};
     }
-    double M[3][3];
+    const dfl Om[3] = {df_of(y[10]), df_of(y[11]), df_of(y[12])};
+    const dfl L[3] = {df_mul(df_of(c.xJ[0]), Om[0]), df_mul(df_of(c.xJ[1]), Om[1]), df_mul(df_of(c.xJ[2]), Om[2])};
+    dfl gyro[3];
+    df_cross(Om, L, gyro);
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            double a = 0.0, b = 0.0;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                a += Rd[k][i] * R[k][j];
-                b += R[k][i] * Rd[k][j];
-            }
-            M[i][j] = a - b;
-        }
-    const double eR[3] = {0.5 * M[2][1], 0.5 * M[0][2], 0.5 * M[1][0]};
-    const double Om[3] = {y[10], y[11], y[12]};
-    const double L[3] = {c.dJ[0] * Om[0], c.dJ[1] * Om[1], c.dJ[2] * Om[2]};
-    double gyro[3];
-    dcross(Om, L, gyro);
-    rhs[0] = f_coll;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) rhs[j + 1] = c.dJ[j] * (-c.dKatt[j] * eR[j] - c.dKom[j] * Om[j]) + gyro[j];
+    for (int j = 0; j < 3; ++j)
+        rhs[j + 1] = df_sub(gyro[j], df_add(df_mul(df_of(c.xJKatt[j]), eR[j]), df_mul(df_of(c.xJKom[j]), Om[j])));
 }
 
 // Desired rotor speeds from the selected controller.
@@ -251,13 +279,7 @@ __device__ __forceinline__ void controller(const DynConsts& c, const float y[17]
     }
     dfl rhs[4];
     if (c.controller == 2 || c.controller == 3) {
-        double r[4];
-        geometric_rhs(c, y, u, c.controller == 3, r);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float hi = (float)r[j];
-            rhs[j] = {hi, (float)(r[j] - (double)hi)};
-        }
+        geometric_rhs(c, y, u, c.controller == 3, rhs);
     } else {
         ctbr_rhs(c, y + 10, u, rhs);
     }
