@@ -267,7 +267,11 @@ __device__ void geometric_rhs(const DynConsts& c, const float y[17], const float
         rhs[j + 1] = df_sub(gyro[j], df_add(df_mul(df_of(c.xJKatt[j]), eR[j]), df_mul(df_of(c.xJKom[j]), Om[j])));
 }
 
-// Desired rotor speeds from the selected controller.
+// Desired rotor speeds from the selected controller.  GEO = false leaves the
+// geometric controllers (LV, PS) out at compile time: their law is several
+// times the size of the CTBR and SRT paths, and each launch fetches its code
+// from a cold instruction cache.
+template <bool GEO>
 __device__ __forceinline__ void controller(const DynConsts& c, const float y[17], const float u[4],
                                            float omega_des[4], CtrlTape* tape) {
     if (c.controller == 1) {
@@ -278,11 +282,10 @@ __device__ __forceinline__ void controller(const DynConsts& c, const float y[17]
         return;
     }
     dfl rhs[4];
-    if (c.controller == 2 || c.controller == 3) {
+    if (GEO && (c.controller == 2 || c.controller == 3))
         geometric_rhs(c, y, u, c.controller == 3, rhs);
-    } else {
+    else
         ctbr_rhs(c, y + 10, u, rhs);
-    }
     allocate(c, rhs, omega_des, tape);
 }
 
@@ -320,10 +323,11 @@ __device__ __forceinline__ void rhs(const DynConsts& c, const float y[13], float
 }
 
 // Controller, rotor lag and thrust/moment of one sub-step.
+template <bool GEO>
 __device__ __forceinline__ void rotors(const DynConsts& c, float y[17], const float u[4], float& Fz, float eta[3],
                                        CtrlTape* tape) {
     float wd[4];
-    controller(c, y, u, wd, tape);
+    controller<GEO>(c, y, u, wd, tape);
     Fz = 0.0f;
     eta[0] = eta[1] = eta[2] = 0.0f;
 #pragma unroll
@@ -338,9 +342,10 @@ __device__ __forceinline__ void rotors(const DynConsts& c, float y[17], const fl
     }
 }
 
+template <bool GEO = false>
 __device__ __forceinline__ void substep(const DynConsts& c, float y[17], const float u[4]) {
     float Fz, eta[3];
-    rotors(c, y, u, Fz, eta, nullptr);
+    rotors<GEO>(c, y, u, Fz, eta, nullptr);
     const float h = c.h;
     if (c.integrator == 1) {
         float k1[13];
@@ -376,8 +381,9 @@ __device__ __forceinline__ void substep(const DynConsts& c, float y[17], const f
     for (int j = 6; j < 10; ++j) y[j] *= qn;
 }
 
+template <bool GEO = false>
 __device__ __forceinline__ void control_step(const DynConsts& c, float y[17], const float u[4]) {
-    for (int s = 0; s < c.n_sub; ++s) substep(c, y, u);
+    for (int s = 0; s < c.n_sub; ++s) substep<GEO>(c, y, u);
 }
 
 // ---------------------------------------------------------------- adjoint
@@ -484,7 +490,7 @@ __device__ void substep_record(const DynConsts& c, const float y_in[17], const f
 #pragma unroll
     for (int j = 0; j < 17; ++j) y[j] = y_in[j];
     float eta[3];
-    rotors(c, y, u, T.Fz, eta, &T.ctrl);
+    rotors<false>(c, y, u, T.Fz, eta, &T.ctrl);
 #pragma unroll
     for (int i = 0; i < 4; ++i) T.w[i] = y[13 + i];
     const float h = c.h;
@@ -737,6 +743,7 @@ __device__ __forceinline__ void load_cmd(const float* __restrict__ u_, int n, in
     for (int j = 0; j < 4; ++j) u[j] = u_[(size_t)j * n + a];
 }
 
+template <bool GEO>
 __global__ void __launch_bounds__(128) step_kernel(DynConsts c, int n, float* state, const float* __restrict__ cmd,
                                                    float* __restrict__ ckpt) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -745,7 +752,7 @@ __global__ void __launch_bounds__(128) step_kernel(DynConsts c, int n, float* st
     load_state(state, n, a, y);
     load_cmd(cmd, n, a, u);
     if (ckpt) store_state(ckpt, n, a, y);
-    control_step(c, y, u);
+    control_step<GEO>(c, y, u);
     store_state(state, n, a, y);
 }
 
@@ -765,6 +772,7 @@ __global__ void __launch_bounds__(128) step_backward_kernel(DynConsts c, int n, 
     for (int j = 0; j < 4; ++j) g_cmd[(size_t)j * n + a] = gu[j];
 }
 
+template <bool GEO>
 __global__ void __launch_bounds__(128) rollout_kernel(DynConsts c, int n, int T, int K,
                                                       const float* __restrict__ state0,
                                                       const float* __restrict__ cmds, float* __restrict__ states_out,
@@ -777,7 +785,7 @@ __global__ void __launch_bounds__(128) rollout_kernel(DynConsts c, int n, int T,
     for (int t = 0; t < T; ++t) {
         if (ckpt && t % K == 0) store_state(ckpt + (size_t)(t / K) * 17 * n, n, a, y);
         load_cmd(cmds + (size_t)t * 4 * n, n, a, u);
-        control_step(c, y, u);
+        control_step<GEO>(c, y, u);
         if (states_out) store_state(states_out + (size_t)(t + 1) * 17 * n, n, a, y);
     }
     if (state_final) store_state(state_final, n, a, y);
@@ -847,12 +855,14 @@ inline unsigned blocks_for(int n, int bs) { return (unsigned)((n + bs - 1) / bs)
 
 cudaError_t launch_step(const DynConsts& c, int n, float* state, const float* cmd, float* ckpt, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    step_kernel<<<blocks_for(n, 128), 128, 0, s>>>(c, n, state, cmd, ckpt);
+    if (c.controller >= 2) step_kernel<true><<<blocks_for(n, 128), 128, 0, s>>>(c, n, state, cmd, ckpt);
+    else step_kernel<false><<<blocks_for(n, 128), 128, 0, s>>>(c, n, state, cmd, ckpt);
     return cudaGetLastError();
 }
 
 cudaError_t launch_step_backward(const DynConsts& c, int n, const float* state_in, const float* cmd,
                                  const float* g_out, float* g_in, float* g_cmd, cudaStream_t s) {
+    if (c.controller >= 2) return cudaErrorInvalidValue;  // the adjoint kernels carry the CTBR and SRT laws only
     if (n == 0) return cudaSuccess;
     step_backward_kernel<<<blocks_for(n, 128), 128, 0, s>>>(c, n, state_in, cmd, g_out, g_in, g_cmd);
     return cudaGetLastError();
@@ -861,7 +871,11 @@ cudaError_t launch_step_backward(const DynConsts& c, int n, const float* state_i
 cudaError_t launch_rollout(const DynConsts& c, int n, int T, int K, const float* state0, const float* cmds,
                            float* states_out, float* ckpt, float* state_final, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    rollout_kernel<<<blocks_for(n, 128), 128, 0, s>>>(c, n, T, K, state0, cmds, states_out, ckpt, state_final);
+    if (c.controller >= 2)
+        rollout_kernel<true><<<blocks_for(n, 128), 128, 0, s>>>(c, n, T, K, state0, cmds, states_out, ckpt, state_final);
+    else
+        rollout_kernel<false><<<blocks_for(n, 128), 128, 0, s>>>(c, n, T, K, state0, cmds, states_out, ckpt,
+                                                                 state_final);
     return cudaGetLastError();
 }
 
@@ -870,6 +884,7 @@ size_t rollout_tape_bytes(int n, int K) { return sizeof(float) * kTapeWords * (s
 cudaError_t launch_rollout_backward(const DynConsts& c, int n, int T, int K, const float* ckpt, const float* cmds,
                                     const float* g_states, float* g_state0, float* g_cmds, float* tape,
                                     cudaStream_t s) {
+    if (c.controller >= 2) return cudaErrorInvalidValue;
     if (n == 0) return cudaSuccess;
     rollout_backward_kernel<<<blocks_for(n, 64), 64, 0, s>>>(c, n, T, K, ckpt, cmds, g_states, g_state0, g_cmds,
                                                              tape);
