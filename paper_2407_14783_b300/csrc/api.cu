@@ -188,6 +188,12 @@ int derive(const sim_params& p, DynConsts& d, CamConsts& cam) {
         (p.k[2] == 0 && p.k[1] == 0) || p.k[2] < 0 || p.k[1] < 0 || p.controller < 0 || p.controller > 3)
         return fail(SIM_ERR_INVALID_ARG, "invalid sim_params");
     memset(&d, 0, sizeof(d));
+    // FP64 values of the controller constants; the kernels get them as
+    // double-float pairs (the x* fields)
+    struct {
+        double dJ[3], dJK[3], drate_max[3], dhalf_a_max_m, dAinv[4][4], df_lo, df_hi, dk[3], domega_min, domega_max;
+        double dmass, dg, dKpos[3], dKvel[3], dKatt[3], dKom[3];
+    } w{};
     d.mass = p.mass;
     d.inv_mass = (float)(1.0 / p.mass);
     for (int j = 0; j < 3; ++j) {
@@ -234,60 +240,60 @@ int derive(const sim_params& p, DynConsts& d, CamConsts& cam) {
     for (int r = 0; r < 4; ++r)
         for (int c = 0; c < 4; ++c) {
             d.Ainv[r][c] = (float)M[r][4 + c];
-            d.dAinv[r][c] = M[r][4 + c];
+            w.dAinv[r][c] = M[r][4 + c];
         }
     for (int j = 0; j < 3; ++j) {
-        d.dJ[j] = p.J[j];
-        d.dJK[j] = (double)p.J[j] * p.K_rate[j];
-        d.drate_max[j] = p.rate_max[j];
-        d.dk[j] = p.k[j];
+        w.dJ[j] = p.J[j];
+        w.dJK[j] = (double)p.J[j] * p.K_rate[j];
+        w.drate_max[j] = p.rate_max[j];
+        w.dk[j] = p.k[j];
     }
-    d.dhalf_a_max_m = 0.5 * (double)p.a_max * p.mass;
+    w.dhalf_a_max_m = 0.5 * (double)p.a_max * p.mass;
     d.controller = p.controller;
-    d.dmass = p.mass;
-    d.dg = p.g;
+    w.dmass = p.mass;
+    w.dg = p.g;
     for (int j = 0; j < 3; ++j) {
-        d.dKpos[j] = p.K_pos[j];
-        d.dKvel[j] = p.K_vel[j];
-        d.dKatt[j] = p.K_att[j];
-        d.dKom[j] = p.K_omega[j];
+        w.dKpos[j] = p.K_pos[j];
+        w.dKvel[j] = p.K_vel[j];
+        w.dKatt[j] = p.K_att[j];
+        w.dKom[j] = p.K_omega[j];
     }
-    d.domega_min = p.omega_min;
-    d.domega_max = p.omega_max;
+    w.domega_min = p.omega_min;
+    w.domega_max = p.omega_max;
     d.k0 = p.k[0];
     d.k1 = p.k[1];
     d.k2 = p.k[2];
     auto thrust = [&](double w) { return (double)p.k[2] * w * w + (double)p.k[1] * w + (double)p.k[0]; };
     d.f_lo = (float)thrust(p.omega_min);
     d.f_hi = (float)thrust(p.omega_max);
-    d.df_lo = thrust(p.omega_min);
-    d.df_hi = thrust(p.omega_max);
+    w.df_lo = thrust(p.omega_min);
+    w.df_hi = thrust(p.omega_max);
     // double-float pairs of the controller constants (hi + lo == the double to ~48 bits)
     auto pair = [](double v) {
         const float hi = (float)v;
         return make_float2(hi, (float)(v - (double)hi));
     };
     for (int j = 0; j < 3; ++j) {
-        d.xJ[j] = pair(d.dJ[j]);
-        d.xJK[j] = pair(d.dJK[j]);
-        d.xrate_max[j] = pair(d.drate_max[j]);
+        d.xJ[j] = pair(w.dJ[j]);
+        d.xJK[j] = pair(w.dJK[j]);
+        d.xrate_max[j] = pair(w.drate_max[j]);
     }
     for (int r = 0; r < 4; ++r)
-        for (int k = 0; k < 4; ++k) d.xAinv[r][k] = pair(d.dAinv[r][k]);
-    d.xhalf_a_max_m = pair(d.dhalf_a_max_m);
-    d.xf_lo = pair(d.df_lo);
-    d.xf_hi = pair(d.df_hi);
-    d.xk0 = pair(d.dk[0]);
-    d.xk1sq = pair(d.dk[1] * d.dk[1]);
-    d.x4k2 = pair(4.0 * d.dk[2]);
-    d.xhalf_f_hi = pair(0.5 * d.df_hi);
+        for (int k = 0; k < 4; ++k) d.xAinv[r][k] = pair(w.dAinv[r][k]);
+    d.xhalf_a_max_m = pair(w.dhalf_a_max_m);
+    d.xf_lo = pair(w.df_lo);
+    d.xf_hi = pair(w.df_hi);
+    d.xk0 = pair(w.dk[0]);
+    d.xk1sq = pair(w.dk[1] * w.dk[1]);
+    d.x4k2 = pair(4.0 * w.dk[2]);
+    d.xhalf_f_hi = pair(0.5 * w.df_hi);
     for (int j = 0; j < 3; ++j) {
-        d.xmKpos[j] = pair(d.dmass * d.dKpos[j]);
-        d.xmKvel[j] = pair(d.dmass * d.dKvel[j]);
-        d.xJKatt[j] = pair(d.dJ[j] * d.dKatt[j]);
-        d.xJKom[j] = pair(d.dJ[j] * d.dKom[j]);
+        d.xmKpos[j] = pair(w.dmass * w.dKpos[j]);
+        d.xmKvel[j] = pair(w.dmass * w.dKvel[j]);
+        d.xJKatt[j] = pair(w.dJ[j] * w.dKatt[j]);
+        d.xJKom[j] = pair(w.dJ[j] * w.dKom[j]);
     }
-    d.xmg = pair(d.dmass * d.dg);
+    d.xmg = pair(w.dmass * w.dg);
     d.omega_min = p.omega_min;
     d.omega_max = p.omega_max;
     const double h = (double)p.dt / p.n_sub;

@@ -33,13 +33,10 @@ struct DynConsts {
     // Near zero rotor thrust the square-root inverse of the thrust polynomial
     // turns FP32 rounding of the mixer solve (about 1e-6 N) into rotor-speed
     // errors of order 1 rad/s, so the controller carries its cancellation-prone
-    // quantities in double precision, as double-float pairs (x* below: hi + lo
-    // floats, about 48 bits, on the FP32 pipes) formed on the host from the
-    // FP64 values (d* below).
-    double dJ[3], dJK[3], drate_max[3], dhalf_a_max_m, dAinv[4][4], df_lo, df_hi, dk[3], domega_min, domega_max;
+    // quantities in double precision, as double-float pairs (hi + lo floats,
+    // about 48 bits, on the FP32 pipes) formed on the host from FP64 values.
     float2 xJ[3], xJK[3], xrate_max[3], xhalf_a_max_m, xAinv[4][4], xf_lo, xf_hi, xk0, xk1sq, x4k2, xhalf_f_hi;
     int controller;                 // 0 CTBR, 1 SRT, 2 LV, 3 PS
-    double dmass, dg, dKpos[3], dKvel[3], dKatt[3], dKom[3];
     // geometric controllers: m K_pos, m K_vel, m g, J K_att, J K_omega
     float2 xmKpos[3], xmKvel[3], xmg, xJKatt[3], xJKom[3];
     float decay;                    // exp(-c h)
