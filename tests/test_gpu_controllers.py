@@ -75,3 +75,25 @@ def test_srt_adjoint_and_geometric_backward_refused(make_sim, oracle_mod, wl):
     lv = make_sim(wl.params(controller=2))
     with pytest.raises(SimError):
         lv.step_backward(to_soa(s), to_soa(u), to_soa(g))
+
+
+@pytest.mark.parametrize("ctrl", [2, 3])
+def test_geometric_rollout_launch(make_sim, oracle_mod, wl, ctrl):
+    """sim_rollout with LV / PS (the kernels' geometric instantiation): one launch
+    over T steps reproduces T sim_step launches bit for bit, and the oracle
+    within the dynamics tolerance."""
+    from paper_2407_14783_b300.sim import to_soa, from_soa
+    p = wl.params(controller=ctrl)
+    sc = wl.room_scene()
+    n, T, K = 150, 40, 8
+    s = wl.spawn_states(sc, n, 60 + ctrl, 1107.0).astype(np.float32)
+    u = _cmds(wl, ctrl, T, n, s, 61 + ctrl).astype(np.float32)
+    sim = make_sim(p)
+    states, ckpt, final = sim.rollout(to_soa(s), torch.stack([to_soa(x) for x in u]), K=K)
+    torch.cuda.synchronize()
+    sim.check()
+    got = np.stack([from_soa(states[t]) for t in range(T + 1)])
+    assert np.array_equal(got, _gpu_rollout(sim, s, u))
+    assert np.array_equal(from_soa(final), got[-1])
+    ref = oracle_mod.rollout(p, s.astype(np.float64), u.astype(np.float64))
+    assert dyn_error(got, ref)[..., 0:13].max() <= DYN_TOL
