@@ -100,6 +100,37 @@ __device__ __forceinline__ dfl df_sqrt(dfl a) {
     const dfl rem = df_sub(a, dfl{p, __fmaf_rn(s, s, -p)});
     return df_norm(s, __fmul_rn(rem.hi, __frcp_rn(__fmul_rn(2.0f, s))));
 }
+// 1/n! as double-float pairs, n = 0 .. 17
+__constant__ float2 kInvFact[18] = {
+    {0x1p+0f, 0.0f}, {0x1p+0f, 0.0f}, {0x1p-1f, 0.0f}, {0x1.555556p-3f, -0x1.555556p-28f},
+    {0x1.555556p-5f, -0x1.555556p-30f}, {0x1.111112p-7f, -0x1.dddddep-32f}, {0x1.6c16c2p-10f, -0x1.27d27ep-35f},
+    {0x1.a01a02p-13f, -0x1.7f97fap-39f}, {0x1.a01a02p-16f, -0x1.7f97fap-42f}, {0x1.71de3ap-19f, 0x1.55b1ccp-45f},
+    {0x1.27e4fcp-22f, -0x1.10ec14p-47f}, {0x1.ae6456p-26f, 0x1.fd5138p-52f}, {0x1.1eed8ep-29f, 0x1.ff1b12p-54f},
+    {0x1.612462p-33f, -0x1.8af25ep-58f}, {0x1.93974ap-37f, 0x1.180f94p-62f}, {0x1.ae7f3ep-41f, 0x1.ccee08p-67f},
+    {0x1.ae7f3ep-45f, 0x1.ccee08p-71f}, {0x1.952c78p-49f, -0x1.f9ea56p-74f}};
+// sin a and cos a of a float angle as double-float pairs.  Cody-Waite
+// reduction r = a - k pi/2 with pi/2 = P1 + P2 + P3 in three floats (each
+// product k Pi is exact as an FMA pair), then the Taylor series of sin and
+// cos on |r| <= pi/4, Horner in r^2 up to r^17 / 17!, and the quadrant of k.
+// Absolute error below 1e-14 for |a| < 1e6 against FP64 sin and cos.
+__device__ __forceinline__ void df_sincos(float a, dfl& sa, dfl& ca) {
+    const float k = rintf(a * 0x1.45f306p-1f);
+    dfl r = df_sub(df_of(a), df_mul(df_of(k), df_of(0x1.921fb6p+0f)));
+    r = df_sub(r, df_mul(df_of(k), df_of(-0x1.777a5cp-25f)));
+    r = df_sub(r, df_mul(df_of(k), df_of(-0x1.ee59dap-50f)));
+    const dfl x = df_mul(r, r);
+    dfl ps = df_of(kInvFact[17]), pc = df_of(kInvFact[16]);
+#pragma unroll
+    for (int j = 7; j >= 0; --j) {
+        const dfl fs = df_of(kInvFact[2 * j + 1]), fc = df_of(kInvFact[2 * j]);
+        ps = df_add(df_mul(ps, x), (j & 1) ? df_neg(fs) : fs);
+        pc = df_add(df_mul(pc, x), (j & 1) ? df_neg(fc) : fc);
+    }
+    const dfl sr = df_mul(r, ps);
+    const int q = (int)k & 3;
+    sa = q == 0 ? sr : q == 1 ? pc : q == 2 ? df_neg(sr) : df_neg(pc);
+    ca = q == 0 ? pc : q == 1 ? df_neg(sr) : q == 2 ? df_neg(pc) : sr;
+}
 __device__ __forceinline__ dfl df_dot3(const dfl a[3], const dfl b[3]) {
     return df_add(df_add(df_mul(a[0], b[0]), df_mul(a[1], b[1])), df_mul(a[2], b[2]));
 }
@@ -186,12 +217,12 @@ __device__ __forceinline__ void ctbr_rhs(const DynConsts& c, const float Om[3], 
 // collective thrust = its projection on body z; desired attitude from the
 // force direction and the yaw command; moment from the attitude and rate
 // errors plus the gyroscopic term.  u = (target, yaw) in m or m/s and rad.
-// On double-float pairs like the CTBR law; only the yaw's sine and cosine are
-// taken in FP64.  R is used unnormalised (Rr = |q|^2 R): the collective thrust
+// On double-float pairs like the CTBR law, the yaw's sine and cosine
+// included.  R is used unnormalised (Rr = |q|^2 R): the collective thrust
 // and the attitude error are linear in it and take the 1/|q|^2 at the end.
 __device__ void geometric_rhs(const DynConsts& c, const float y[17], const float u[4], bool position, dfl rhs[4]) {
-    double sy_d, cy_d;
-    sincos((double)u[3], &sy_d, &cy_d);
+    dfl sy, cy;
+    df_sincos(u[3], sy, cy);
     const float w = y[6], x = y[7], yq = y[8], z = y[9];
     auto pr = [](float a, float b) { return df_mul(df_of(a), df_of(b)); };  // exact
     const dfl ww = pr(w, w), xx = pr(x, x), yy = pr(yq, yq), zz = pr(z, z);
@@ -226,8 +257,6 @@ __device__ void geometric_rhs(const DynConsts& c, const float y[17], const float
 #pragma unroll
         for (int k = 0; k < 3; ++k) b3[k] = df_mul(F[k], r);
     }
-    const float sy_hi = (float)sy_d, cy_hi = (float)cy_d;
-    const dfl sy = {sy_hi, (float)(sy_d - (double)sy_hi)}, cy = {cy_hi, (float)(cy_d - (double)cy_hi)};
     const dfl zero = df_of(0.0f);
     const dfl c1[3] = {cy, sy, zero};
     dfl b2[3];
