@@ -97,3 +97,20 @@ def test_geometric_rollout_launch(make_sim, oracle_mod, wl, ctrl):
     assert np.array_equal(from_soa(final), got[-1])
     ref = oracle_mod.rollout(p, s.astype(np.float64), u.astype(np.float64))
     assert dyn_error(got, ref)[..., 0:13].max() <= DYN_TOL
+
+
+def test_geometric_yaw_far_from_zero(make_sim, oracle_mod, wl):
+    """LV with yaw commands shifted by up to +-60 whole turns: the GPU reduces the
+    angle by pi/2 on its own (every quadrant and large quadrant counts), the
+    oracle takes FP64 sin and cos of the same float command."""
+    p = wl.params(controller=2)
+    sc = wl.room_scene()
+    n, T = 200, 60
+    s = wl.spawn_states(sc, n, 95, 1107.0).astype(np.float32)
+    u = _cmds(wl, 2, T, n, s, 96)
+    turns = np.random.default_rng(97).integers(-60, 61, n)
+    u[:, :, 3] += 2.0 * np.pi * turns[None, :]
+    u = u.astype(np.float32)
+    ref = oracle_mod.rollout(p, s.astype(np.float64), u.astype(np.float64))
+    got = _gpu_rollout(make_sim(p), s, u)
+    assert dyn_error(got, ref)[..., 0:13].max() <= DYN_TOL
