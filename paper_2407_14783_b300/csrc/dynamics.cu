@@ -73,8 +73,16 @@ __device__ __forceinline__ dfl df_add(dfl a, dfl b) {
     const dfl u = df_norm(s.hi, __fadd_rn(s.lo, t.hi));
     return df_norm(u.hi, __fadd_rn(u.lo, t.lo));
 }
+// a + b with one two-sum on the high parts: error about 2^-44 relative to
+// the operands (not to the result), for sums whose result need not keep full
+// precision under cancellation
+__device__ __forceinline__ dfl df_add_fast(dfl a, dfl b) {
+    const dfl s = df_two_sum(a.hi, b.hi);
+    return df_norm(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
 __device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ dfl df_sub_fast(dfl a, dfl b) { return df_add_fast(a, df_neg(b)); }
 __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
     const float p = __fmul_rn(a.hi, b.hi);
     const float e = __fmaf_rn(a.hi, b.hi, -p);
@@ -123,8 +131,8 @@ __device__ __forceinline__ void df_sincos(float a, dfl& sa, dfl& ca) {
 #pragma unroll
     for (int j = 7; j >= 0; --j) {
         const dfl fs = df_of(kInvFact[2 * j + 1]), fc = df_of(kInvFact[2 * j]);
-        ps = df_add(df_mul(ps, x), (j & 1) ? df_neg(fs) : fs);
-        pc = df_add(df_mul(pc, x), (j & 1) ? df_neg(fc) : fc);
+        ps = df_add_fast(df_mul(ps, x), (j & 1) ? df_neg(fs) : fs);
+        pc = df_add_fast(df_mul(pc, x), (j & 1) ? df_neg(fc) : fc);
     }
     const dfl sr = df_mul(r, ps);
     const int q = (int)k & 3;
@@ -132,13 +140,13 @@ __device__ __forceinline__ void df_sincos(float a, dfl& sa, dfl& ca) {
     ca = q == 0 ? pc : q == 1 ? df_neg(sr) : q == 2 ? df_neg(pc) : sr;
 }
 __device__ __forceinline__ dfl df_dot3(const dfl a[3], const dfl b[3]) {
-    return df_add(df_add(df_mul(a[0], b[0]), df_mul(a[1], b[1])), df_mul(a[2], b[2]));
+    return df_add_fast(df_add_fast(df_mul(a[0], b[0]), df_mul(a[1], b[1])), df_mul(a[2], b[2]));
 }
 // a x b
 __device__ __forceinline__ void df_cross(const dfl a[3], const dfl b[3], dfl r[3]) {
-    r[0] = df_sub(df_mul(a[1], b[2]), df_mul(a[2], b[1]));
-    r[1] = df_sub(df_mul(a[2], b[0]), df_mul(a[0], b[2]));
-    r[2] = df_sub(df_mul(a[0], b[1]), df_mul(a[1], b[0]));
+    r[0] = df_sub_fast(df_mul(a[1], b[2]), df_mul(a[2], b[1]));
+    r[1] = df_sub_fast(df_mul(a[2], b[0]), df_mul(a[0], b[2]));
+    r[2] = df_sub_fast(df_mul(a[0], b[1]), df_mul(a[1], b[0]));
 }
 
 // ---------------------------------------------------------------- thrust allocation
@@ -227,27 +235,27 @@ __device__ void geometric_rhs(const DynConsts& c, const float y[17], const float
     auto pr = [](float a, float b) { return df_mul(df_of(a), df_of(b)); };  // exact
     const dfl ww = pr(w, w), xx = pr(x, x), yy = pr(yq, yq), zz = pr(z, z);
     const dfl xy = pr(x, yq), wz = pr(w, z), xz = pr(x, z), wy = pr(w, yq), yz = pr(yq, z), wx = pr(w, x);
-    const dfl inv_n = df_div(df_of(1.0f), df_add(df_add(ww, xx), df_add(yy, zz)));
+    const dfl inv_n = df_div(df_of(1.0f), df_add_fast(df_add_fast(ww, xx), df_add_fast(yy, zz)));
     dfl Rr[3][3];
-    Rr[0][0] = df_sub(df_add(ww, xx), df_add(yy, zz));
-    Rr[0][1] = df_twice(df_sub(xy, wz));
-    Rr[0][2] = df_twice(df_add(xz, wy));
-    Rr[1][0] = df_twice(df_add(xy, wz));
-    Rr[1][1] = df_sub(df_add(ww, yy), df_add(xx, zz));
-    Rr[1][2] = df_twice(df_sub(yz, wx));
-    Rr[2][0] = df_twice(df_sub(xz, wy));
-    Rr[2][1] = df_twice(df_add(yz, wx));
-    Rr[2][2] = df_sub(df_add(ww, zz), df_add(xx, yy));
+    Rr[0][0] = df_sub_fast(df_add_fast(ww, xx), df_add_fast(yy, zz));
+    Rr[0][1] = df_twice(df_sub_fast(xy, wz));
+    Rr[0][2] = df_twice(df_add_fast(xz, wy));
+    Rr[1][0] = df_twice(df_add_fast(xy, wz));
+    Rr[1][1] = df_sub_fast(df_add_fast(ww, yy), df_add_fast(xx, zz));
+    Rr[1][2] = df_twice(df_sub_fast(yz, wx));
+    Rr[2][0] = df_twice(df_sub_fast(xz, wy));
+    Rr[2][1] = df_twice(df_add_fast(yz, wx));
+    Rr[2][2] = df_sub_fast(df_add_fast(ww, zz), df_add_fast(xx, yy));
     dfl F[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         if (position)
-            F[j] = df_neg(df_add(df_mul(df_of(c.xmKpos[j]), df_two_sum(y[j], -u[j])),
+            F[j] = df_neg(df_add_fast(df_mul(df_of(c.xmKpos[j]), df_two_sum(y[j], -u[j])),
                                  df_mul(df_of(c.xmKvel[j]), df_of(y[3 + j]))));
         else
             F[j] = df_neg(df_mul(df_of(c.xmKvel[j]), df_two_sum(y[3 + j], -u[j])));
     }
-    F[2] = df_add(F[2], df_of(c.xmg));
+    F[2] = df_add_fast(F[2], df_of(c.xmg));
     const dfl col2[3] = {Rr[0][2], Rr[1][2], Rr[2][2]};
     rhs[0] = df_mul(df_dot3(F, col2), inv_n);
     dfl b3[3] = {df_of(0.0f), df_of(0.0f), df_of(1.0f)};
@@ -280,10 +288,10 @@ __device__ void geometric_rhs(const DynConsts& c, const float y[17], const float
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
         const int i = I[e], j = J[e];
-        dfl m = df_sub(df_mul(bcol[i][0], Rr[0][j]), df_mul(Rr[0][i], bcol[j][0]));
+        dfl m = df_sub_fast(df_mul(bcol[i][0], Rr[0][j]), df_mul(Rr[0][i], bcol[j][0]));
 #pragma unroll
         for (int k = 1; k < 3; ++k)
-            m = df_add(m, df_sub(df_mul(bcol[i][k], Rr[k][j]), df_mul(Rr[k][i], bcol[j][k])));
+            m = df_add_fast(m, df_sub_fast(df_mul(bcol[i][k], Rr[k][j]), df_mul(Rr[k][i], bcol[j][k])));
         const dfl mn = df_mul(m, inv_n);
         eR[e] = {__fmul_rn(0.5f, mn.hi), __fmul_rn(0.5f, mn.lo)};
     }
@@ -293,7 +301,7 @@ __device__ void geometric_rhs(const DynConsts& c, const float y[17], const float
     df_cross(Om, L, gyro);
 #pragma unroll
     for (int j = 0; j < 3; ++j)
-        rhs[j + 1] = df_sub(gyro[j], df_add(df_mul(df_of(c.xJKatt[j]), eR[j]), df_mul(df_of(c.xJKom[j]), Om[j])));
+        rhs[j + 1] = df_sub_fast(gyro[j], df_add_fast(df_mul(df_of(c.xJKatt[j]), eR[j]), df_mul(df_of(c.xJKom[j]), Om[j])));
 }
 
 // Desired rotor speeds from the selected controller.  GEO = false leaves the
