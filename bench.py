@@ -32,6 +32,9 @@ sys.path.insert(0, ROOT)
 from paper_2407_14783_b300 import workloads as wl  # noqa: E402
 
 METRIC = "agent-frames/s (dynamics+64x64 depth/RGB) on 1 B300"
+BATCHED_LOOPS = 3                 # timed 100-step graph launches of the batched leg
+SERVE_LOAD, SERVE_SECONDS = 0.5, 2.0  # the serving leg: half the offered load, 2 s of arrivals
+BUILD_SCENE = (2_000_000, 901)    # (triangles, seed) of the scene whose build phases are timed
 EPISODE = 25
 E2E_WARMUP_S = 0.5
 N_AGENTS = 256
@@ -163,11 +166,21 @@ def run_reference(args):
     return 0
 
 
-def cpu_baseline_leg(p, scene, w_h, u_h, budget_s=15.0):
-    """Oracle (as it stands) on a bounded sample of the same workload."""
+def cpu_baseline_leg(p, scene, w_h, u_h, count_states=None, budget_s=15.0):
+    """Oracle (as it stands) on a bounded sample of the same workload.  With
+    count_states ([n, 17], the poses of the GPU's counted launch) it also walks
+    the oracle's own median-split BVH for every ray of those images and reports
+    the mean internal nodes and triangles per ray beside the GPU's counts."""
     import oracle
     oracle.build()
     osc = oracle.Scene.from_workload(scene)
+    walk = None
+    if count_states is not None:
+        walk = osc.traversal_counts(p, count_states)
+        walk["rays"] = int(count_states.shape[0] * p["width"] * p["height"])
+        walk["what"] = ("closest-hit walks, nearer child first, of the oracle's median-split BVH (leaves of up to "
+                        "4 triangles, large triangles inside the tree): mean internal nodes visited and "
+                        "triangles tested per ray")
     sample = 8
     spawn = wl.spawn_states(scene, sample, 3, w_h)
     cmds = wl.hover_commands(1000, sample, 4, u_h)
@@ -198,7 +211,7 @@ def cpu_baseline_leg(p, scene, w_h, u_h, budget_s=15.0):
     return {"value": sample * n / t_used, "unit": "agent-frames/s", "cores": oracle.num_threads(),
             "kind": "oracle",
             "sample": f"{n} steps x {sample} agents of the 208,812-triangle room (dynamics + render, FP64)",
-            "tiny_config_agent_frames_per_s": tiny_s}
+            "tiny_config_agent_frames_per_s": tiny_s, "oracle_bvh_per_ray": walk}
 
 
 def _recorded_profile():
@@ -483,10 +496,18 @@ def run_ours(args):
            "warmup": f"at least 3 steps and {E2E_WARMUP_S} s of steps before the timed steps",
            "value_env_step": one_shot}
 
+    # the batched and serving legs' scenes (and a 2M-triangle scene whose build
+    # is timed) are generated on host cores while the GPU runs the extras below
+    legs = ws == 1 and not args.no_extra_legs
+    if legs:
+        b_specs, s_specs = batched_specs(), serving_specs()
+        pool = ScenePool(b_specs + s_specs + [BUILD_SCENE])
+
     # traversal counters of one launch -> algorithmic bytes of the ray-cast kernel
     state.copy_(spawn)
     sim.step(state, cmds[W])
     cnt = sim.render(ids, state, depth, rgb, counted=True)
+    counted_states = state.T.double().cpu().numpy()   # the oracle's BVH walks the same rays (cpu_baseline leg)
     render_ms = statistics.mean(ren_ms)
     roof = raycast_roofline(sim, cnt, n, p, render_ms)
     clocks = clk.summary()
@@ -531,11 +552,36 @@ def run_ours(args):
             "extras": {"nearest_obstacle": {"agents": n, "ms": near_ms, "queries_per_s": n / (near_ms * 1e-3)},
                        "sensors": sensors, "controllers": controllers},
             "clocks": clocks}
+    line["extras"]["build_ms"] = {"triangles_%d" % scene.n_tris: sim.scene_build_times(sid)}
+    sim.close()
+    if legs:
+        # the bounded batched and serving legs of the same metric (sub-records)
+        scenes_all = pool.result()
+        pool.close()
+        nb, ns = len(b_specs), len(s_specs)
+        big = scenes_all[-1]
+        with Sim(p) as bsim:
+            bid = bsim.add_workload_scene(big)
+            line["extras"]["build_ms"]["triangles_%d" % big.n_tris] = bsim.scene_build_times(bid)
+        line["extras"]["build_ms"]["note"] = ("device time between stream events at the build's phase "
+                                              "boundaries; wall = host time of sim_create_scene")
+        bl = batched_leg(p, scenes_all[:nb], BATCHED_LOOPS, 1, compare_fixed=False)
+        bl["workload"] = BATCHED_WORKLOAD
+        bl["note"] = "%d timed graph launches of 100 steps after 1 warm-up launch" % BATCHED_LOOPS
+        line["batched"] = bl
+        sv = serving_leg(p, scenes_all[nb:nb + ns], loads=(SERVE_LOAD,), duration=SERVE_SECONDS)
+        lv = sv["levels"][str(SERVE_LOAD)]
+        line["serving"] = {"workload": SERVING_WORKLOAD, "load": SERVE_LOAD, "seconds_of_arrivals": SERVE_SECONDS,
+                           **lv, "capacity_agents": sv["capacity_agents"],
+                           "triangles_total": sv["triangles_total"], "bvh_build_s": sv["bvh_build_s"]}
+        line["p50_ms"], line["p99_ms"] = lv["p50_ms"], lv["p99_ms"]
+        line["extras"]["scene_generation"] = {"scenes": len(scenes_all), "workers": pool.workers,
+                                              "wall_s": pool.wall_s}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_leg(p, scene, w_h, u_h)
+        line["cpu_baseline"] = cpu_baseline_leg(p, scene, w_h, u_h, counted_states)
+        line["roofline"]["per_ray"]["oracle_median_split"] = line["cpu_baseline"]["oracle_bvh_per_ray"]
     if rank == 0:
         print(json.dumps(line), flush=True)
-    sim.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0
@@ -566,32 +612,90 @@ def multi_scene_cpu_baseline(p, scenes, w_h, u_h, n_pick=8, agents=2, steps=20, 
             "oracle_bvh_build_s": build_s}
 
 
-def batched_scenes(n_scenes=64, lo=10_000, hi=1_000_000, seed=99):
-    """64 procedural scenes with log-uniform triangle counts (seeds 100..163)."""
+BATCHED_WORKLOAD = ("batched multi-scene: 64 scenes of 10k-1M triangles (log-uniform), 4,096 agents by Zipf(1.1), "
+                    "100-step graph-captured loop, 64x64 depth+RGB")
+SERVING_WORKLOAD = ("serving: 32 resident scenes of 50k-2M triangles, Poisson arrivals, 1-1024 agents x 1-16 steps "
+                    "per request, last 64x64 depth+RGB returned")
+
+
+def batched_specs(n_scenes=64, lo=10_000, hi=1_000_000, seed=99):
+    """(triangles, seed) of the 64 procedural scenes with log-uniform triangle
+    counts (seeds 100..163)."""
     sizes = wl.Rng(seed).log_uniform(lo, hi, n_scenes)
-    return [wl.sized_scene(int(t), 100 + i) for i, t in enumerate(sizes)]
+    return [(int(t), 100 + i) for i, t in enumerate(sizes)]
 
 
-def run_batched(args):
-    """Batched multi-scene workload: 64 scenes of 10k-1M triangles, 4,096 agents
-    spread by Zipf(1.1), one persistent render per step, 100-step graph-captured
-    loop; autotuned render configuration against the fixed 8x4 one."""
+def serving_specs():
+    """(triangles, seed) of the 32 resident scenes of 50k-2M triangles (seeds 500..531)."""
+    sizes = wl.Rng(5).log_uniform(50_000, 2_000_000, 32)
+    return [(int(t), 500 + i) for i, t in enumerate(sizes)]
+
+
+class ScenePool:
+    """Procedural scenes generated in spawned worker processes while the GPU
+    works on something else.  The generator is plain numpy (no GPU, no CUDA
+    state in the workers); spawn, not fork, because the parent holds a CUDA
+    context."""
+
+    def __init__(self, specs, workers=None):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        workers = workers or max(1, min(len(specs), (os.cpu_count() or 2) - 2, 12))
+        self.t0 = time.time()
+        self.ex = cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+        self.futs = [self.ex.submit(wl.sized_scene, t, sd) for t, sd in specs]
+        self.workers = workers
+
+    def result(self, lo=0, hi=None):
+        out = [f.result() for f in self.futs[lo:hi]]
+        self.wall_s = time.time() - self.t0
+        return out
+
+    def close(self):
+        self.ex.shutdown(wait=True, cancel_futures=True)
+
+
+BATCHED_AGENTS = 4096
+
+
+def batched_groups(scenes, counts, w_h, pieces=None):
+    """Spawn states of the batched workload: agent j of scene s is spawn state j
+    of the seeded set of scene s, so a rank that runs agents first..first+count-1
+    of a scene gets exactly the states the single-GPU run gives them.  pieces =
+    [(scene, first, count)] (default: every agent of every scene); scenes maps a
+    scene number to its mesh.  Returns [(scene, states [count, 17])]."""
+    if pieces is None:
+        pieces = [(s, 0, int(k)) for s, k in enumerate(counts)]
+    return [(s, wl.spawn_states(scenes[s], int(counts[s]), 1000 + s, w_h)[a:a + c]) for s, a, c in pieces]
+
+
+def batched_leg(p, scenes, steps, warmup, compare_fixed=True, iters_tune=3, groups=None, dist_ws=1, counts=None):
+    """The batched multi-scene workload: 4,096 agents spread over the scenes by
+    Zipf(1.1), one persistent render per step inside a graph-captured 100-step
+    loop.  Returns the measurements (agent-frames/s of the autotuned
+    configuration, and of the fixed 8x4 one when compare_fixed).  groups: this
+    rank's [(scene, spawn states)] (default: all agents of all scenes); under
+    torchrun (dist_ws > 1) every rank times its own groups and the value is the
+    agents of all ranks over the slowest rank's time."""
     import torch
     from paper_2407_14783_b300.sim import Sim, to_soa
-    p = wl.params()
     w_h, u_h = _hover(p)
+    T = 100
+    if counts is None:
+        counts = wl.zipf_partition(BATCHED_AGENTS, len(scenes), 1.1, 7)
+    if groups is None:
+        groups = batched_groups(scenes, counts, w_h)
+    sim = Sim(p, device=torch.cuda.current_device())
     t0 = time.time()
-    scenes = batched_scenes()
-    gen_s = time.time() - t0
-    n_agents, T = 4096, 100
-    counts = wl.zipf_partition(n_agents, len(scenes), 1.1, 7)
-    sim = Sim(p)
-    t0 = time.time()
-    sids = [sim.add_workload_scene(sc) for sc in scenes]
+    used = sorted({s for s, _ in groups})
+    sid_of = {s: sim.add_workload_scene(scenes[s]) for s in used}
+    sids = list(sid_of.values())
+    torch.cuda.synchronize()
     build_s = time.time() - t0
-    spawn = np.concatenate([wl.spawn_states(sc, int(k), 1000 + i, w_h) for i, (sc, k) in enumerate(zip(scenes, counts))])
-    spawn = to_soa(spawn)
-    ids = torch.tensor(np.repeat(sids, counts), dtype=torch.int32, device="cuda")
+    spawn = to_soa(np.concatenate([st for _, st in groups]))
+    n_agents = spawn.shape[1]
+    ids = torch.tensor(np.concatenate([np.full(len(st), sid_of[s]) for s, st in groups]), dtype=torch.int32,
+                       device="cuda")
     cmds = torch.tensor(np.ascontiguousarray(wl.hover_commands(T, n_agents, 4, u_h).astype(np.float32)
                                              .transpose(0, 2, 1)), device="cuda")
     F = 2
@@ -599,18 +703,22 @@ def run_batched(args):
     rgb = torch.empty((F, n_agents, p["height"], p["width"], 3), dtype=torch.uint8, device="cuda")
     state = spawn.clone()
     fixed = sim.render_config()
-    best, times = sim.autotune(ids, state, depth[0], rgb[0], iters=3)
+    best, times = sim.autotune(ids, state, depth[0], rgb[0], iters=iters_tune)
     results = {}
-    for name, cfg in (("fixed_8x4", fixed), ("autotuned", best)):
+    for name, cfg in ((("fixed_8x4", fixed),) if compare_fixed else ()) + (("autotuned", best),):
         sim.set_render_config(cfg)
         loop = sim.make_loop(ids, state, cmds, depth, rgb)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             state.copy_(spawn)
             loop.launch()
         torch.cuda.synchronize()
+        if dist_ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
         evs = []
-        with ClockSampler(0) as clk:
-            for _ in range(args.steps):
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            for _ in range(steps):
                 state.copy_(spawn)   # every timed loop starts from the spawn states (outside the events)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
@@ -620,34 +728,84 @@ def run_batched(args):
             torch.cuda.synchronize()
         sim.check()
         ms = [a.elapsed_time(b) for a, b in evs]
-        results[name] = {"clk": clk.summary()}
-        results[name]["ms_per_loop"] = statistics.mean(ms)
-        results[name]["value"] = n_agents * T / (statistics.mean(ms) * 1e-3)
+        frames, secs = n_agents * T * steps, sum(ms) * 1e-3
+        if dist_ws > 1:
+            from paper_2407_14783_b300.shard import reduce_step_metrics
+            frames, secs = reduce_step_metrics(frames, secs)
+        results[name] = {"clk": clk.summary(), "ms_per_loop": 1e3 * secs / steps, "value": frames / secs}
         loop.close()
-    sim.set_render_config(best)
-    total_tris = int(sum(sc.n_tris for sc in scenes))
-    line = {"metric": METRIC, "value": results["autotuned"]["value"], "unit": "agent-frames/s", "n_gpus": 1,
-            "steps": args.steps * T, "warmup": args.warmup * T,
-            "ms_per_step": results["autotuned"]["ms_per_loop"] / T, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic (64 procedural scenes, seeded)",
-            "config": {"workload": "batched multi-scene: 64 scenes of 10k-1M triangles (log-uniform), 4,096 agents "
-                                   "by Zipf(1.1), 100-step graph-captured loop, 64x64 depth+RGB",
-                       "scenes": len(scenes), "triangles_total": total_tris,
-                       "triangles_min_max": [int(min(sc.n_tris for sc in scenes)),
-                                             int(max(sc.n_tris for sc in scenes))],
-                       "agents_per_scene_min_max": [int(counts.min()), int(counts.max())],
-                       "l2": "inputs larger than L2 (scene BVHs %.2f GB)" % (
-                           sum(sim.scene_info(i)["bytes"] for i in sids) / 1e9),
-                       "fixed_config": fixed, "autotuned_config": best,
-                       "fixed_value": results["fixed_8x4"]["value"],
-                       "autotuned_over_fixed": results["autotuned"]["value"] / results["fixed_8x4"]["value"],
-                       "scene_generation_s": gen_s, "bvh_build_s": build_s},
-            "gpu_launches": args.steps * T * 2,
-            "clocks": results["autotuned"]["clk"]}
-    if not getattr(args, "no_cpu_baseline", False):
-        line["cpu_baseline"] = multi_scene_cpu_baseline(p, scenes, w_h, u_h)
-    print(json.dumps(line), flush=True)
+    out = {"value": results["autotuned"]["value"], "unit": "agent-frames/s",
+           "ms_per_step": results["autotuned"]["ms_per_loop"] / T, "loops": steps, "warmup_loops": warmup,
+           "steps_per_loop": T, "agents": n_agents, "scenes": len(used),
+           "triangles_total": int(sum(scenes[s].n_tris for s in used)),
+           "triangles_min_max": [int(min(scenes[s].n_tris for s in used)), int(max(scenes[s].n_tris for s in used))],
+           "agents_per_scene_min_max": [int(counts.min()), int(counts.max())],
+           "scene_bytes": int(sum(sim.scene_info(i)["bytes"] for i in sids)),
+           "bvh_depth_max": int(max(sim.scene_info(i)["depth"] for i in sids)),
+           "autotuned_config": best, "bvh_build_s": build_s, "clocks": results["autotuned"]["clk"],
+           "gpu_launches": steps * T * 2}
+    if compare_fixed:
+        out["fixed_config"] = fixed
+        out["fixed_value"] = results["fixed_8x4"]["value"]
+        out["autotuned_over_fixed"] = results["autotuned"]["value"] / results["fixed_8x4"]["value"]
     sim.close()
+    return out
+
+
+def run_batched(args):
+    """Batched multi-scene workload: 64 scenes of 10k-1M triangles, 4,096 agents
+    spread by Zipf(1.1), one persistent render per step, 100-step graph-captured
+    loop; autotuned render configuration against the fixed 8x4 one.  Under
+    torchrun every rank builds and runs only its part of the plan_shards split
+    (whole scenes, heavy scenes split by agents; no data-path collective)."""
+    import torch
+    ws, rank, local = _dist()
+    p = wl.params()
+    w_h, u_h = _hover(p)
+    specs = batched_specs()
+    counts = wl.zipf_partition(BATCHED_AGENTS, len(specs), 1.1, 7)
+    if ws > 1:
+        import torch.distributed as dist
+        from paper_2407_14783_b300.shard import rank_workload
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        # an agent's render cost grows with the depth of its scene's BVH
+        mine, pieces = rank_workload(counts, ws, rank, [math.log(t) for t, _ in specs])
+    else:
+        mine, pieces = list(range(len(specs))), None
+    t0 = time.time()
+    pool = ScenePool([specs[s] for s in mine])
+    scenes = dict(zip(mine, pool.result()))
+    pool.close()
+    gen_s = time.time() - t0
+    groups = batched_groups(scenes, counts, w_h, pieces)
+    r = batched_leg(p, scenes, args.steps, args.warmup, compare_fixed=ws == 1, groups=groups, dist_ws=ws,
+                    counts=counts)
+    line = {"metric": METRIC, "value": r["value"], "unit": "agent-frames/s", "n_gpus": ws,
+            "steps": args.steps * r["steps_per_loop"], "warmup": args.warmup * r["steps_per_loop"],
+            "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "strong" if ws > 1 else "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (64 procedural scenes, seeded)",
+            "config": {"workload": BATCHED_WORKLOAD, "scenes": len(specs),
+                       "triangles_total": int(sum(t for t, _ in specs)) if ws > 1 else r["triangles_total"],
+                       "triangles_min_max": r["triangles_min_max"],
+                       "agents_per_scene_min_max": r["agents_per_scene_min_max"],
+                       "l2": "inputs larger than L2 (scene BVHs %.2f GB on rank 0)" % (r["scene_bytes"] / 1e9),
+                       "autotuned_config": r["autotuned_config"],
+                       "scene_generation_s": gen_s, "bvh_build_s": r["bvh_build_s"],
+                       "bvh_depth_max": r["bvh_depth_max"],
+                       "parallelism": "scene/agent shards (plan_shards), rank 0: %d scenes, %d agents" % (
+                           r["scenes"], r["agents"]) if ws > 1 else "single GPU"},
+            "gpu_launches": r["gpu_launches"], "clocks": r["clocks"]}
+    if ws == 1:
+        line["config"].update({"fixed_config": r["fixed_config"], "fixed_value": r["fixed_value"],
+                               "autotuned_over_fixed": r["autotuned_over_fixed"]})
+        if not getattr(args, "no_cpu_baseline", False):
+            line["cpu_baseline"] = multi_scene_cpu_baseline(p, [scenes[s] for s in mine], w_h, u_h)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
     return 0
 
 
@@ -824,23 +982,19 @@ class _PinnedArena:
         return self.buf[start:start + n].view(dtype).view(*shape)
 
 
-def run_serving(args):
-    """Serving workload: 32 resident scenes of 50k-2M triangles; Poisson arrivals
-    (mean 2,000 requests/s at load 1.0), each request n ~ log-U[1, 1024] agents of one
-    scene for U{1..16} steps, returning the final state and the last 64x64
-    depth + RGB; throughput and p50 / p99 latency at loads 0.25, 0.5 and 1.0."""
+def serving_leg(p, scenes, loads=(0.25, 0.5, 1.0), duration=3.0, rate=2000.0, cap=8192):
+    """The serving workload: the scenes stay resident; Poisson arrivals (mean
+    `rate` requests/s at load 1.0), each request n ~ log-U[1, 1024] agents of one
+    scene for U{1..16} steps, returning the final state and the last 64x64 depth
+    + RGB.  Throughput and p50 / p99 request latency per load level."""
     import torch
     from paper_2407_14783_b300.serve import Server
     from paper_2407_14783_b300.sim import Sim
-    p = wl.params()
     w_h, u_h = _hover(p)
-    t0 = time.time()
-    sizes = wl.Rng(5).log_uniform(50_000, 2_000_000, 32)
-    scenes = [wl.sized_scene(int(t), 500 + i) for i, t in enumerate(sizes)]
-    gen_s = time.time() - t0
     sim = Sim(p)
+    t0 = time.time()
     sids = [sim.add_workload_scene(sc) for sc in scenes]
-    cap = 8192
+    build_s = time.time() - t0
     srv = Server(sim, capacity=cap)
     # per-scene pools of spawn states and commands (requests use the first n agents)
     pool_s = [np.ascontiguousarray(wl.spawn_states(sc, 1024, 600 + i, w_h).astype(np.float32).T)
@@ -848,17 +1002,15 @@ def run_serving(args):
     pool_u = np.ascontiguousarray(wl.hover_commands(16, 1024, 7, u_h).astype(np.float32).transpose(0, 2, 1))
     arena = _PinnedArena(6 << 30)
     H, W = p["height"], p["width"]
-    rate = 2000.0
-    duration = float(args.serve_seconds)
     levels = {}
-
     lat = {}
 
     def release(ticket):
         if ticket not in lat:
             lat[ticket] = srv.wait(ticket, 600000)
 
-    for li, load in enumerate((0.25, 0.5, 1.0)):
+    for load in loads:
+        li = {0.25: 0, 0.5: 1, 1.0: 2}.get(load, 3)
         reqs = wl.poisson_requests(rate * load, duration, len(scenes), 50 + li)
         arena.live.clear()
         arena.head = 0
@@ -897,21 +1049,66 @@ def run_serving(args):
                                                   max(1, st1["iterations"] - st0["iterations"]),
                              "wall_s": wall}
     srv.close()
+    sim.close()
+    return {"levels": levels, "triangles_total": int(sum(sc.n_tris for sc in scenes)), "capacity_agents": cap,
+            "seconds_per_load": duration, "bvh_build_s": build_s}
+
+
+def run_serving(args):
+    """Serving workload: 32 resident scenes of 50k-2M triangles; Poisson arrivals
+    (mean 2,000 requests/s at load 1.0), each request n ~ log-U[1, 1024] agents of one
+    scene for U{1..16} steps, returning the final state and the last 64x64
+    depth + RGB; throughput and p50 / p99 latency at loads 0.25, 0.5 and 1.0."""
+    p = wl.params()
+    w_h, u_h = _hover(p)
+    t0 = time.time()
+    pool = ScenePool(serving_specs())
+    scenes = pool.result()
+    pool.close()
+    gen_s = time.time() - t0
+    r = serving_leg(p, scenes, duration=float(args.serve_seconds))
+    levels = r["levels"]
     full = levels["1.0"]
     line = {"metric": "agent-frames/s served (dynamics+64x64 depth/RGB) on 1 B300; p50/p99 step latency",
             "value": full["throughput_agent_frames_per_s"], "unit": "agent-frames/s", "n_gpus": 1,
             "steps": sum(v["requests"] for v in levels.values()), "warmup": 0,
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic (32 procedural scenes, Poisson request stream, seeded)",
-            "config": {"workload": "serving: 32 resident scenes of 50k-2M triangles, Poisson arrivals, "
-                                   "1-1024 agents x 1-16 steps per request, last 64x64 depth+RGB returned",
-                       "triangles_total": int(sum(sc.n_tris for sc in scenes)), "capacity_agents": cap,
-                       "seconds_per_load": duration, "scene_generation_s": gen_s},
+            "config": {"workload": SERVING_WORKLOAD, "triangles_total": r["triangles_total"],
+                       "capacity_agents": r["capacity_agents"], "seconds_per_load": r["seconds_per_load"],
+                       "scene_generation_s": gen_s, "bvh_build_s": r["bvh_build_s"]},
             "served": levels, "p50_ms": full["p50_ms"], "p99_ms": full["p99_ms"]}
     if not getattr(args, "no_cpu_baseline", False):
         line["cpu_baseline"] = multi_scene_cpu_baseline(p, scenes, w_h, u_h)
     print(json.dumps(line), flush=True)
-    sim.close()
+    return 0
+
+
+def run_build(args):
+    """Scene builds alone: the 208,812-triangle room and a 2M-triangle scene,
+    each built --steps times after --warmup builds; CUDA-event time per build
+    phase (mean over the timed builds) and the host time of the whole call."""
+    import torch
+    from paper_2407_14783_b300.sim import Sim
+    p = wl.params()
+    out = {}
+    for name, scene in (("triangles_208812", make_workload(0)[1]), ("triangles_2M", wl.sized_scene(*BUILD_SCENE))):
+        with Sim(p) as sim:
+            runs = []
+            for k in range(args.warmup + args.steps):
+                sid = sim.add_workload_scene(scene)
+                torch.cuda.synchronize()
+                if k >= args.warmup:
+                    runs.append(sim.scene_build_times(sid))
+                sim.remove_scene(sid)
+            out[name] = {ph: statistics.mean(r[ph] for r in runs) for ph in runs[0]}
+            out[name]["n_tris"] = int(scene.n_tris)
+    line = {"metric": "scene build time (ms)", "value": out["triangles_208812"]["wall"], "unit": "ms",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "dtype": "f32", "data": "synthetic (procedural scenes, seeded)",
+            "config": {"workload": "BVH builds of the 208,812-triangle room and a 2M-triangle scene"},
+            "build_ms": out}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -923,8 +1120,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--no-autotune", action="store_true", help="use the default ray-cast configuration")
+    ap.add_argument("--no-extra-legs", action="store_true",
+                    help="skip the bounded batched and serving legs and the 2M-triangle build of the default run")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="seconds of arrivals per load level")
-    ap.add_argument("--workload", choices=["large", "batched", "diff", "serving", "swarm"], default="large",
+    ap.add_argument("--workload", choices=["large", "batched", "diff", "serving", "swarm", "build"], default="large",
                     help="large: single 208,812-triangle scene, 256 agents (default); batched: 64 scenes, "
                          "4,096 agents, graph-captured 100-step loop (--steps counts loops)")
     args = ap.parse_args()
@@ -940,6 +1139,8 @@ def main():
         return run_swarm(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "build":
+        return run_build(args)
     return run_ours(args)
 
 

@@ -109,9 +109,13 @@ int sim_destroy_ctx(sim_ctx* ctx);
 /* Replace the context's parameters (affects calls enqueued afterwards). */
 int sim_set_params(sim_ctx* ctx, const sim_params* p);
 
-/* Upload a mesh and build its device BVH (Sec. III-B scenes; the BVH is an
- * LBVH: 30-bit Morton codes of triangle centroids, radix sort, binary radix
- * tree by longest common prefix, bottom-up AABB refit).
+/* Upload a mesh and build its device BVH (Sec. III-B scenes).  The build
+ * sorts the triangle centroids' 30-bit Morton codes (radix sort), builds the
+ * binary radix tree by longest common prefix (Karras 2012) and refits its boxes
+ * bottom-up, then rebuilds the tree above the radix tree's leaves of at most 3
+ * triangles by PLOC clustering (Meister and Bittner 2018) and packs it in
+ * depth-first order; triangles larger than a quarter of the scene extent stay
+ * outside the tree.
  *   verts host float32 [n_verts][3]; tris host int32 [n_tris][3] (vertex
  *   indices, validated); rgb host uint8 [n_tris][3] (flat colour per triangle).
  * On success *scene_id_out receives the id used by sim_render.  The host
@@ -132,6 +136,19 @@ typedef struct sim_scene_info {
     int64_t bytes;
 } sim_scene_info;
 int sim_scene_info_get(const sim_ctx* ctx, int32_t scene_id, sim_scene_info* info);
+
+/* Where a scene's build spent its time (Sec. III-B scene set-up; no timing is
+ * printed in the paper).  phase_ms host float [SIM_BUILD_PHASES] receives the
+ * device time between stream events at the phase boundaries, in order:
+ * 0 triangle and scene bounds, 1 centroid bounds and 30-bit Morton codes,
+ * 2 radix sort, 3 radix tree (Karras 2012), 4 bottom-up refit, 5 clustering
+ * rounds (PLOC, Meister and Bittner 2018), 6 tree packing (binary and 4-wide
+ * nodes), 7 triangle and colour packing.  A phase's time includes the host
+ * read-back that ends it; phases a scene skips read 0.  wall_ms (host float,
+ * nullable) receives the host time of the whole sim_create_scene call.
+ * Errors: INVALID_ARG (null context or phase_ms), NOT_FOUND. */
+#define SIM_BUILD_PHASES 8
+int sim_scene_build_times(const sim_ctx* ctx, int32_t scene_id, float* phase_ms, float* wall_ms);
 
 /* One control step of n agents (Sec. III-A): for each of n_sub sub-steps,
  * body-rate controller -> rotor lag (Eq. 4) -> thrust and moment (Eq. 3) ->
@@ -173,7 +190,10 @@ int sim_render_scene(sim_ctx* ctx, int32_t n_agents, int32_t scene_id, const flo
  * its counters before rendering, so calls whose work overlaps on the GPU (other
  * streams, other contexts on the same device) race: serialise them.
  * Errors: INVALID_ARG when n_agents > SIM_RENDER_STATIC_MAX_AGENTS or < 0,
- * NOT_FOUND for an unknown scene, CUDA for a launch failure. */
+ * or when sim_render_scene would reject the call (null pointers, a BVH deeper
+ * than the traversal stack); NOT_FOUND for an unknown scene, also with
+ * n_agents = 0; CUDA for a launch failure.  Every check runs before the shared
+ * array is written, so a rejected call leaves it as it was. */
 #define SIM_RENDER_STATIC_MAX_AGENTS 65536
 int sim_render_scene_static(sim_ctx* ctx, int32_t n_agents, int32_t scene_id, const float* state, float* depth,
                             uint8_t* rgb, int32_t* hit_id, void* stream);

@@ -82,6 +82,7 @@ def lib():
             L.oracle_scene_destroy.argtypes = [vp]
             L.oracle_scene_bvh_nodes.restype = i64
             L.oracle_scene_bvh_nodes.argtypes = [vp]
+            L.oracle_traversal_counts.argtypes = [vp, P(OracleParams), i64, dp, dp]
             L.oracle_render.argtypes = [vp, P(OracleParams), i64, dp, ctypes.c_int, dp, P(ctypes.c_uint8),
                                         P(ctypes.c_int32), P(ctypes.c_uint8)]
             L.oracle_validate.argtypes = [vp, P(OracleParams), i64, dp, i64, P(ctypes.c_int64),
@@ -224,6 +225,20 @@ class Scene:
         if rc:
             raise ValueError(f"oracle_render failed ({rc})")
         return {"depth": depth, "rgb": rgb, "id": hid, "tie": tie.astype(bool)}
+
+    def traversal_counts(self, p: dict, states: np.ndarray) -> dict:
+        """Mean per ray, over every pixel of the agents' images, of the internal
+        nodes and triangles a closest-hit walk of this scene's median-split BVH
+        visits and tests (nearer child first).  A statistic, not a parity value."""
+        if not self.bvh:
+            raise ValueError("traversal counts need the oracle's BVH")
+        states = _f64(states)
+        out = np.zeros(2)
+        rc = lib().oracle_traversal_counts(self.handle, ctypes.byref(make_params(p)), states.shape[0],
+                                           _ptr(states, ctypes.c_double), _ptr(out, ctypes.c_double))
+        if rc:
+            raise ValueError(f"oracle_traversal_counts failed ({rc})")
+        return {"nodes": float(out[0]), "tris": float(out[1])}
 
     def nearest(self, positions: np.ndarray, max_dist: float):
         """Closest mesh point of every query point: (dist [n], point [n,3], tri [n])."""

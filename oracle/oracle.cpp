@@ -772,6 +772,67 @@ int render_impl(const OracleScene* s, const OracleParams* p, int64_t n, const do
     return 0;
 }
 
+// Entry distance of the ray into a box no farther than t_lim, or -1 when it
+// misses (exact slab test; a zero direction component keeps the slab open
+// when the origin lies inside it).
+double box_entry(const double o[3], const double inv[3], const double lo[3], const double hi[3], double t_lim) {
+    double t0 = 0.0, t1 = t_lim;
+    for (int j = 0; j < 3; ++j) {
+        double a = (lo[j] - o[j]) * inv[j], b = (hi[j] - o[j]) * inv[j];
+        if (std::isnan(a) || std::isnan(b)) {
+            if (o[j] < lo[j] || o[j] > hi[j]) return -1.0;
+            continue;
+        }
+        if (a > b) std::swap(a, b);
+        t0 = std::max(t0, a);
+        t1 = std::min(t1, b);
+        if (t0 > t1) return -1.0;
+    }
+    return t0;
+}
+
+// Work of one ray's closest-hit walk over the oracle's median-split BVH: the
+// internal nodes it visits (the root, then every child whose box it enters
+// before its current closest hit, nearer child first) and the triangles of the
+// leaves it reaches.  A statistic to set beside the GPU's counted walks, not a
+// parity quantity.
+void walk_counts(const OracleScene& s, const double o[3], const double d[3], double t_max, int64_t& nodes,
+                 int64_t& tests) {
+    if (s.nodes.empty()) return;
+    double inv[3];
+    for (int j = 0; j < 3; ++j) inv[j] = 1.0 / d[j];
+    double best = t_max;
+    std::vector<std::pair<int32_t, double>> stack;
+    stack.push_back({0, 0.0});
+    while (!stack.empty()) {
+        const auto top = stack.back();
+        stack.pop_back();
+        if (top.second > best) continue;
+        const BvhNode& n = s.nodes[top.first];
+        if (n.left < 0) {
+            for (int32_t i = n.first; i < n.first + n.count; ++i) {
+                ++tests;
+                Hit h;
+                if (moller_trumbore(o, d, s.tris[s.order[i]], h) && h.m >= 0.0 && h.t > kTmin && h.t <= best)
+                    best = h.t;
+            }
+            continue;
+        }
+        ++nodes;
+        const double tl = box_entry(o, inv, s.nodes[n.left].lo, s.nodes[n.left].hi, best);
+        const double tr = box_entry(o, inv, s.nodes[n.right].lo, s.nodes[n.right].hi, best);
+        const bool l_first = tl >= 0.0 && (tr < 0.0 || tl <= tr);
+        // the farther child goes on the stack first
+        if (l_first) {
+            if (tr >= 0.0) stack.push_back({n.right, tr});
+            stack.push_back({n.left, tl});
+        } else {
+            if (tl >= 0.0) stack.push_back({n.left, tl});
+            if (tr >= 0.0) stack.push_back({n.right, tr});
+        }
+    }
+}
+
 int validate_impl(const OracleScene* s, const OracleParams* p, int64_t n, const double* states, const Swarm* sw,
                   int64_t npix, const int64_t* pix, const int32_t* id, const float* depth, uint8_t* valid) {
     if (!s || !p || n < 0) return -1;
@@ -950,6 +1011,30 @@ int oracle_render(const void* scene, const OracleParams* p, int64_t n, const dou
                   double* depth, uint8_t* rgb, int32_t* hit_id, uint8_t* tie) {
     return render_impl(static_cast<const OracleScene*>(scene), p, n, states, use_bvh, nullptr, depth, rgb, hit_id,
                        tie);
+}
+
+// Mean per ray of the internal nodes visited and the triangles tested by
+// closest-hit walks over the oracle's median-split BVH (walk_counts), for every
+// pixel of the n agents' images.  states [n][17]; out[0] nodes, out[1] triangles.
+int oracle_traversal_counts(const void* scene, const OracleParams* p, int64_t n, const double* states,
+                            double* out) {
+    const OracleScene* s = static_cast<const OracleScene*>(scene);
+    if (!s || !p || n < 0 || !out) return -1;
+    if (s->nodes.empty() && !s->tris.empty()) return -2;
+    const int W = p->width, H = p->height;
+    const int64_t npix = n * (int64_t)W * H;
+    int64_t nodes = 0, tests = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : nodes, tests)
+    for (int64_t k = 0; k < npix; ++k) {
+        const int64_t a = k / ((int64_t)W * H);
+        const int r = (int)((k / W) % H), c = (int)(k % W);
+        double o[3], d[3];
+        camera_ray(*p, states + a * 17, r, c, o, d);
+        walk_counts(*s, o, d, p->max_depth, nodes, tests);
+    }
+    out[0] = npix ? (double)nodes / (double)npix : 0.0;
+    out[1] = npix ? (double)tests / (double)npix : 0.0;
+    return 0;
 }
 
 // As oracle_render, with the n agents forming one swarm [Sec. III-B]: every

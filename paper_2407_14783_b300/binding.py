@@ -110,6 +110,7 @@ SIGNATURES = {
     "sim_create_scene": [_vp, _vp, _i64, _vp, _i64, _vp, _P(_i32), _vp],
     "sim_destroy_scene": [_vp, _i32],
     "sim_scene_info_get": [_vp, _i32, _P(SceneInfo)],
+    "sim_scene_build_times": [_vp, _i32, _P(ctypes.c_float), _P(ctypes.c_float)],
     "sim_step": [_vp, _i32, _vp, _vp, _vp, _vp],
     "sim_render": [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
     "sim_render_scene": [_vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp],

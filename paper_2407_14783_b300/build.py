@@ -48,13 +48,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(out_dir, exist_ok=True)
     objs = []
     procs = []
+    headers = [d for d in _deps() if d.endswith((".h", ".cuh", ".py"))]
+    newest_header = max(os.path.getmtime(h) for h in headers)
     for src in sources():
         obj = os.path.join(out_dir, os.path.basename(src) + ".o")
+        objs.append(obj)
+        # an object is reused when it is newer than its source and every header
+        if not force and not verbose and os.path.exists(obj) and \
+                os.path.getmtime(obj) >= max(os.path.getmtime(src), newest_header):
+            continue
         cmd = [NVCC, *FLAGS, "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT), src))
-        objs.append(obj)
     failed = []
     for p, src in procs:
         out, _ = p.communicate()

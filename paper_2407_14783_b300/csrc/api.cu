@@ -52,6 +52,7 @@ struct SceneRec {
     void* mem[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     size_t bytes = 0;
     int64_t n_tris = 0;
+    float build_wall_ms = 0.0f;  // host time of sim_create_scene, upload to table update
     LbvhResult r{};
 };
 
@@ -730,6 +731,7 @@ int sim_create_scene(sim_ctx* c, const float* verts, int64_t n_verts, const int3
     std::lock_guard<std::mutex> lk(c->mu);
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
+    const auto t_start = std::chrono::steady_clock::now();
     SceneRec rec;
     rec.n_tris = n_tris;
     const size_t vb = sizeof(float) * 3 * std::max<int64_t>(n_verts, 1);
@@ -796,6 +798,8 @@ int sim_create_scene(sim_ctx* c, const float* verts, int64_t n_verts, const int3
         free_scene(c, c->scenes[id]);
         return rc;
     }
+    c->scenes[id].build_wall_ms =
+        std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     *scene_id_out = id;
     return SIM_OK;
 }
@@ -821,6 +825,16 @@ int sim_scene_info_get(const sim_ctx* c, int32_t id, sim_scene_info* info) {
     info->depth = s.r.depth;
     info->leaf_max = kLeafMax;
     info->bytes = (int64_t)s.bytes;
+    return SIM_OK;
+}
+
+int sim_scene_build_times(const sim_ctx* c, int32_t id, float* phase_ms, float* wall_ms) {
+    if (!c || !phase_ms) return fail(SIM_ERR_INVALID_ARG, "null argument");
+    if (id < 0 || id >= (int)c->scenes.size() || !c->scenes[id].live) return fail(SIM_ERR_NOT_FOUND, "no such scene");
+    static_assert(kBuildPhases == SIM_BUILD_PHASES, "phase count of the ABI");
+    const SceneRec& s = c->scenes[id];
+    for (int i = 0; i < kBuildPhases; ++i) phase_ms[i] = s.r.phase_ms[i];
+    if (wall_ms) *wall_ms = s.build_wall_ms;
     return SIM_OK;
 }
 
@@ -1630,12 +1644,15 @@ int ctx_device(const sim_ctx* c) { return c ? c->device : -1; }
 // Render n agents of one scene with caller-supplied scratch: soa_dev holds the
 // scene id of every agent and counters_dev the two work counters, already
 // zero.  Same checks and kernel as sim_render.
+int render_scene_check(sim_ctx* c, int n, int scene_id, const int32_t* soa_dev, const float* state) {
+    if (!c) return fail(SIM_ERR_INVALID_ARG, "null context");
+    if (!ctx_scene_live(c, scene_id)) return fail(SIM_ERR_NOT_FOUND, "no such scene");
+    return check_render_args(c, n, soa_dev, state);
+}
+
 int render_scene_with_scratch(sim_ctx* c, int n, int scene_id, const int32_t* soa_dev, unsigned* counters_dev,
                               const float* state, float* depth, uint8_t* rgb, int32_t* hit, cudaStream_t s) {
-    if (!c) return fail(SIM_ERR_INVALID_ARG, "null context");
-    if (scene_id < 0 || scene_id >= (int)c->scenes.size() || !c->scenes[scene_id].live)
-        return fail(SIM_ERR_NOT_FOUND, "no such scene");
-    int rc = check_render_args(c, n, soa_dev, state);
+    int rc = render_scene_check(c, n, scene_id, soa_dev, state);
     if (rc) return rc;
     if (n == 0) return SIM_OK;
     DeviceGuard g(c->device);

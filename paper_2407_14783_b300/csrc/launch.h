@@ -24,9 +24,15 @@ cudaError_t launch_rollout_backward(const DynConsts& c, int n, int T, int K, con
 size_t rollout_tape_bytes(int n, int K);
 
 // lbvh.cu
+// Phases of a scene build, timed by stream events at their boundaries: scene
+// and triangle bounds, centroid bounds and Morton codes, radix sort, radix
+// tree, refit, clustering rounds (PLOC), tree packing, triangle and colour
+// packing.  A phase's time includes the host read-backs that end it.
+constexpr int kBuildPhases = 8;
 struct LbvhResult {
     float lo[3], hi[3];
     int n_large, n_bvh, n_nodes, depth, root;
+    float phase_ms[kBuildPhases];
     float4* nodes;
     float4* wide;  // 8 float4 per internal node (valid at even depth): the 4-wide layout
     float4* tris;
@@ -126,6 +132,10 @@ cudaError_t launch_render(const RenderArgs& a, const sim_render_config& c, int c
 // api.cu: context helpers for entry points defined in other files.
 void set_last_error(const char* msg);
 int ctx_device(const sim_ctx* c);
+// The checks of render_scene_with_scratch alone (scene, arguments, BVH depth
+// against the traversal stack, launch size), for callers that must validate
+// before touching their scratch.
+int render_scene_check(sim_ctx* c, int n, int scene_id, const int32_t* soa_dev, const float* state);
 int render_scene_with_scratch(sim_ctx* c, int n, int scene_id, const int32_t* soa_dev, unsigned* counters_dev,
                               const float* state, float* depth, uint8_t* rgb, int32_t* hit, cudaStream_t s);
 // nearest.cu

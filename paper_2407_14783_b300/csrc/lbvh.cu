@@ -765,6 +765,33 @@ inline unsigned nb(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
         if (e_ != cudaSuccess) return e_;      \
     } while (0)
 
+// Stream events at the phase boundaries of one build; timing failures only
+// leave the phase times at zero.
+struct PhaseTimer {
+    cudaEvent_t ev[kBuildPhases + 1] = {};
+    int next = 0;
+    bool ok = true;
+    explicit PhaseTimer() {
+        for (auto& e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) ok = false;
+    }
+    ~PhaseTimer() {
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    // mark the end of every phase up to `phase` (phases with no work take 0)
+    void mark(int phase, cudaStream_t s) {
+        while (ok && next <= phase + 1 && next <= kBuildPhases)
+            if (cudaEventRecord(ev[next++], s) != cudaSuccess) ok = false;
+    }
+    void read(float* ms) {
+        for (int i = 0; i < kBuildPhases; ++i) ms[i] = 0.0f;
+        if (!ok || next != kBuildPhases + 1 || cudaEventSynchronize(ev[kBuildPhases]) != cudaSuccess) return;
+        for (int i = 0; i < kBuildPhases; ++i)
+            if (cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]) != cudaSuccess) ms[i] = 0.0f;
+    }
+};
+
 }  // namespace
 
 // Scratch of the clustering, mostly buffers of the radix build that are dead
@@ -788,7 +815,7 @@ struct PlocScratch {
 // tree, which overwrites everything this wrote.
 cudaError_t ploc_build(int n_bvh, const uint32_t* order, const float4* tlo, const float4* thi, const int2* child,
                        const int2* range, const float4* node_lo, const float4* node_hi, const PlocScratch& w,
-                       int* misc, float pad, LbvhResult* out, bool* ok, cudaStream_t s) {
+                       int* misc, float pad, LbvhResult* out, bool* ok, PhaseTimer& timer, cudaStream_t s) {
     *ok = false;
     VF_TRY(cudaMemsetAsync(w.code_at, 0, sizeof(int) * (size_t)n_bvh, s));
     ploc_leaves_kernel<<<nb(n_bvh - 1, 256), 256, 0, s>>>(n_bvh, child, range, w.code_at, w.src_at);
@@ -830,6 +857,7 @@ cudaError_t ploc_build(int n_bvh, const uint32_t* order, const float4* tlo, cons
     }
     const int n_int = m0 - 1;
     if (created != n_int) return cudaSuccess;
+    timer.mark(5, s);
     int root;
     VF_TRY(cudaMemcpyAsync(&root, cur, sizeof(int), cudaMemcpyDeviceToHost, s));
     // buffers of the clustering rounds that are done with
@@ -902,6 +930,8 @@ cudaError_t lbvh_build(int64_t nt, const float* d_verts, const int* d_tris, cons
     pw.c0 = (int*)take(sizeof(int) * n);
     pw.nn = (int*)take(sizeof(int) * n);
 
+    PhaseTimer timer;
+    timer.mark(-1, s);
     init_bounds_kernel<<<1, 32, 0, s>>>(misc);
     init_bounds_kernel<<<1, 32, 0, s>>>(misc + 6);
     VF_TRY(cudaMemsetAsync(misc + 12, 0, 2 * sizeof(int), s));
@@ -916,9 +946,11 @@ cudaError_t lbvh_build(int64_t nt, const float* d_verts, const int* d_tris, cons
         out->hi[j] = unordered(hb[3 + j]);
         ext = fmaxf(ext, out->hi[j] - out->lo[j]);
     }
+    timer.mark(0, s);
     centroid_bounds_kernel<<<nb(n, 256), 256, 0, s>>>(n, tlo, thi, 0.25f * ext, is_large, misc + 6, misc + 12);
     morton_kernel<<<nb(n, 256), 256, 0, s>>>(n, tlo, thi, is_large, misc + 6, keys0, vals0);
     VF_TRY(cudaGetLastError());
+    timer.mark(1, s);
     uint32_t *ka = keys0, *va = vals0, *kb = keys1, *vb = vals1;
     for (int shift = 0; shift < 32; shift += 8) {
         radix_hist_kernel<<<nblocks, kSortThreads, 0, s>>>(n, ka, shift, hist, nblocks);
@@ -931,6 +963,7 @@ cudaError_t lbvh_build(int64_t nt, const float* d_verts, const int* d_tris, cons
     int nl;
     VF_TRY(cudaMemcpyAsync(&nl, misc + 12, sizeof(int), cudaMemcpyDeviceToHost, s));
     VF_TRY(cudaStreamSynchronize(s));
+    timer.mark(2, s);
     const int n_bvh = n - nl;
     out->n_large = nl;
     out->n_bvh = n_bvh;
@@ -939,6 +972,7 @@ cudaError_t lbvh_build(int64_t nt, const float* d_verts, const int* d_tris, cons
     VF_TRY(alloc(alloc_user, out));
     if (n_bvh > 1) {
         hierarchy_kernel<<<nb(n_bvh - 1, 256), 256, 0, s>>>(n_bvh, ka, child, range, parent_int, parent_leaf);
+        timer.mark(3, s);
         VF_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * n_bvh, s));
         refit_kernel<<<nb(n_bvh, 256), 256, 0, s>>>(n_bvh, va, tlo, thi, child, parent_int, parent_leaf, node_lo,
                                                     node_hi, flags, misc + 13);
@@ -948,13 +982,17 @@ cudaError_t lbvh_build(int64_t nt, const float* d_verts, const int* d_tris, cons
         VF_TRY(cudaMemcpyAsync(&rr, range, sizeof(int2), cudaMemcpyDeviceToHost, s));
         VF_TRY(cudaStreamSynchronize(s));
         const int cnt = rr.y - rr.x + 1;
+        timer.mark(4, s);
         bool clustered = false;
         pw.code_at = is_large;  // dead buffers of the radix build
         pw.c1 = (int*)vb;
         pw.keep = ka;
         pw.make = kb;
         if (cnt > kLeafMax)
-            VF_TRY(ploc_build(n_bvh, va, tlo, thi, child, range, node_lo, node_hi, pw, misc, pad, out, &clustered, s));
+            VF_TRY(ploc_build(n_bvh, va, tlo, thi, child, range, node_lo, node_hi, pw, misc, pad, out, &clustered,
+                              timer, s));
+        // a clustering that gave up counts as clustering time; the radix tree is packed instead
+        timer.mark(5, s);
         if (!clustered) {
             pack_nodes_kernel<<<nb(n_bvh - 1, 256), 256, 0, s>>>(n_bvh, va, tlo, thi, child, range, node_lo, node_hi,
                                                                  pad, out->nodes);
@@ -973,12 +1011,16 @@ cudaError_t lbvh_build(int64_t nt, const float* d_verts, const int* d_tris, cons
         out->root = kEmptyRoot;
         out->depth = 0;
     }
+    timer.mark(6, s);
     if (n > 0) {
         pack_tris_kernel<<<nb(n, 256), 256, 0, s>>>(n, n_bvh, va, d_verts, d_tris, out->tris, out->large);
         pack_colors_kernel<<<nb(n, 256), 256, 0, s>>>(n, d_rgb, out->colors);
         VF_TRY(cudaGetLastError());
     }
-    return cudaStreamSynchronize(s);
+    timer.mark(7, s);
+    VF_TRY(cudaStreamSynchronize(s));
+    timer.read(out->phase_ms);
+    return cudaSuccess;
 }
 
 size_t lbvh_scratch_bytes(int64_t nt) {

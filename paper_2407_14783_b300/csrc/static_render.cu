@@ -74,24 +74,37 @@ extern "C" int sim_render_scene_static(sim_ctx* ctx, int32_t n_agents, int32_t s
         vf::set_last_error("sim_render_scene_static: n_agents must be in [0, SIM_RENDER_STATIC_MAX_AGENTS]");
         return SIM_ERR_INVALID_ARG;
     }
+    if (!vf::ctx_scene_live(ctx, scene_id)) {
+        vf::set_last_error("no such scene");
+        return SIM_ERR_NOT_FOUND;
+    }
     if (n_agents == 0) return SIM_OK;
     const int device = vf::ctx_device(ctx);
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != device) cudaSetDevice(device);
+    if (prev != device) {
+        const cudaError_t e = cudaSetDevice(device);
+        if (e != cudaSuccess) {
+            vf::set_last_error(cudaGetErrorString(e));
+            return SIM_ERR_CUDA;
+        }
+    }
     unsigned char* base = nullptr;
     int rc = scratch_address(device, &base);
+    const int32_t* ids = rc == SIM_OK ? reinterpret_cast<const int32_t*>(base + kCounterBytes) : nullptr;
+    unsigned* counters = reinterpret_cast<unsigned*>(base);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // every check the render makes runs before the scratch is touched, so a
+    // rejected call leaves the shared array as it was
+    if (rc == SIM_OK) rc = vf::render_scene_check(ctx, n_agents, scene_id, ids, state);
     if (rc == SIM_OK) {
-        cudaStream_t s = static_cast<cudaStream_t>(stream);
         fill_static_scratch<<<(n_agents + 255) / 256, 256, 0, s>>>(n_agents, scene_id);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
             vf::set_last_error(cudaGetErrorString(e));
             rc = SIM_ERR_CUDA;
         } else {
-            rc = vf::render_scene_with_scratch(ctx, n_agents, scene_id,
-                                               reinterpret_cast<const int32_t*>(base + kCounterBytes),
-                                               reinterpret_cast<unsigned*>(base), state, depth, rgb, hit_id, s);
+            rc = vf::render_scene_with_scratch(ctx, n_agents, scene_id, ids, counters, state, depth, rgb, hit_id, s);
         }
     }
     if (prev >= 0 && prev != device) cudaSetDevice(prev);

@@ -77,6 +77,16 @@ def local_agents(shard: Shard, agents_per_scene) -> list:
     return out
 
 
+def rank_workload(agents_per_scene, world: int, rank: int, scene_cost=None):
+    """The part of a multi-scene workload that one rank runs: the scenes it must
+    build (sorted) and its agent pieces as (scene, first, count), from the same
+    plan on every rank (plan_shards is deterministic), so no exchange is needed
+    to agree on it."""
+    shard = plan_shards(agents_per_scene, world, scene_cost)[rank]
+    pieces = [(s, a, c) for s in shard.scenes for a, c in shard.ranges[s]]
+    return shard.scenes, pieces
+
+
 def reduce_step_metrics(frames: int, seconds: float, group=None):
     """Whole-job agent-frames and the slowest rank's time (max over ranks)."""
     import torch

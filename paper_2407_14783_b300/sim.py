@@ -114,6 +114,17 @@ class Sim:
         B.check(self.L.sim_scene_info_get(self.h, sid, ctypes.byref(info)), "sim_scene_info_get", self.h)
         return {k: int(getattr(info, k)) for k, _ in B.SceneInfo._fields_}
 
+    BUILD_PHASES = ("bounds", "morton", "sort", "radix_tree", "refit", "clustering", "tree_pack", "tri_pack")
+
+    def scene_build_times(self, sid: int) -> dict:
+        """Milliseconds per build phase of scene sid, and the whole call's host time."""
+        ms = (ctypes.c_float * len(self.BUILD_PHASES))()
+        wall = ctypes.c_float()
+        B.check(self.L.sim_scene_build_times(self.h, sid, ms, ctypes.byref(wall)), "sim_scene_build_times", self.h)
+        out = {k: float(v) for k, v in zip(self.BUILD_PHASES, ms)}
+        out["wall"] = float(wall.value)
+        return out
+
     # ------------------------------------------------------------ dynamics
     def step(self, state, cmd, ckpt=None, stream=None):
         n = state.shape[1]

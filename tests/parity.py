@@ -49,3 +49,18 @@ def compare_images(osc, p, states64, depth, rgb, hit, max_tie_frac=0.01):
     assert frac < max_tie_frac, f"ambiguous fraction {frac}"
     return {"pixels": int(tie.size), "ties": int(tie.sum()), "max_depth_rel_err": float(rel.max()) if rel.size else 0.0,
             "tie_id_diff": int(np.count_nonzero((hit != r["id"]) & tie)), "hit_frac": float((r["id"] >= 0).mean())}
+
+
+GRAD_RTOL = 1e-3    # per component, against the FP64 oracle's exact gradient
+GRAD_FLOOR = 1e-3   # components below GRAD_FLOOR * max|ref| are held to the floor
+
+
+def grad_error(g: np.ndarray, ref: np.ndarray, floor: float = GRAD_FLOOR) -> tuple:
+    """Worst per-component error of one agent's gradient:
+    |g_i - ref_i| / max(|ref_i|, floor * max_j |ref_j|).  Returns (worst, index)."""
+    g = np.asarray(g, dtype=np.float64).ravel()
+    ref = np.asarray(ref, dtype=np.float64).ravel()
+    scale = np.maximum(np.abs(ref), floor * max(np.abs(ref).max(), 1e-30))
+    r = np.abs(g - ref) / scale
+    i = int(np.argmax(r))
+    return float(r[i]), i

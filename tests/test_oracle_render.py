@@ -269,3 +269,21 @@ def test_ambiguous_fraction_large_scene(oracle_mod, wl):
     r = sc.render(p, st)
     assert r["tie"].mean() < 0.01
     assert 0.01 < (r["id"] < 0).mean() < 0.5
+
+
+def test_traversal_counts_of_a_single_leaf_and_a_split(oracle_mod, wl):
+    """The oracle's walk statistic: a mesh of at most 4 triangles is one leaf, so
+    every ray visits no internal node and tests exactly those triangles; a scene
+    behind the camera (all rays miss) visits only the root of its tree."""
+    p = wl.params(width=8, height=6)
+    s = np.zeros((2, 17))
+    s[:, 6] = 1.0
+    s[1, 0:3] = (0.3, -0.2, 0.1)
+    v = np.array([[3.0, -1.0, -1.0], [3.0, 1.5, -1.0], [3.0, 0.0, 2.0], [4.0, 0.0, 0.0], [4.0, 1.0, 0.0]])
+    one = oracle_mod.Scene(v, [[0, 1, 2], [1, 3, 4], [0, 3, 4]], [[1, 2, 3]] * 3)
+    c = one.traversal_counts(p, s)
+    assert c == {"nodes": 0.0, "tris": 3.0}
+    bv, bf = wl.box_mesh((-8.0, -1.0, -1.0), (-6.0, 1.0, 1.0))     # 12 triangles behind the camera
+    behind = oracle_mod.Scene(bv, bf, np.zeros((12, 3), np.uint8))
+    c = behind.traversal_counts(p, s)
+    assert c == {"nodes": 1.0, "tris": 0.0}

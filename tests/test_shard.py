@@ -101,3 +101,62 @@ def test_two_rank_gloo_step_and_gather_matches_single_process(tmp_path, oracle_m
         assert np.array_equal(res["state"][i].numpy(), ref[0])
         dref = oracle_mod.Scene.from_workload(scenes[s]).render(p, ref)["depth"][0]
         assert np.array_equal(res["depth"][i].numpy(), dref)
+
+
+def _batched_worker(rank, world, port, out_path):
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import math
+    import torch
+    import torch.distributed as dist
+    from paper_2407_14783_b300 import workloads as wl
+    from paper_2407_14783_b300.shard import rank_workload, plan_shards, reduce_step_metrics
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # the batched workload's split: 64 scenes of log-uniform 10k-1M triangles,
+    # 4,096 agents by Zipf(1.1), cost per agent log(triangles)
+    sizes = wl.Rng(99).log_uniform(10_000, 1_000_000, 64)
+    counts = wl.zipf_partition(4096, 64, 1.1, 7)
+    cost = [math.log(t) for t in sizes]
+    scenes, pieces = rank_workload(counts, world, rank, cost)
+    plan = plan_shards(counts, world, cost)[rank]
+    assert scenes == plan.scenes
+    assert sorted((s, a, c) for s in plan.ranges for a, c in plan.ranges[s]) == sorted(pieces)
+    mine = torch.tensor(pieces, dtype=torch.int64).reshape(-1, 3)
+    n = torch.tensor([mine.shape[0]])
+    sizes_g = [torch.zeros_like(n) for _ in range(world)]
+    dist.all_gather(sizes_g, n)
+    m = int(max(int(x) for x in sizes_g))
+    pad = torch.full((m, 3), -1, dtype=torch.int64)
+    pad[: mine.shape[0]] = mine
+    parts = [torch.zeros_like(pad) for _ in range(world)]
+    dist.all_gather(parts, pad)
+    frames, secs = reduce_step_metrics(int(sum(c for _, _, c in pieces)) * 100, 1.0 + rank)
+    if rank == 0:
+        torch.save({"parts": [p[: int(k)] for p, k in zip(parts, sizes_g)], "frames": frames, "secs": secs,
+                    "counts": torch.tensor(counts)}, out_path)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_batched_split_covers_the_workload(tmp_path):
+    """Each rank of a world-2 gloo group takes its part of the batched workload
+    from the shared plan; together the parts hold every agent of every scene
+    exactly once, and the reduced frame count is the whole workload's."""
+    import torch
+    import torch.multiprocessing as mp
+    out = str(tmp_path / "split.pt")
+    mp.start_processes(_batched_worker, args=(2, _free_port(), out), nprocs=2, start_method="spawn", join=True)
+    res = torch.load(out)
+    counts = res["counts"].numpy()
+    seen = {}
+    for rank_part in res["parts"]:
+        for s, a, c in rank_part.tolist():
+            for j in range(a, a + c):
+                seen[(s, j)] = seen.get((s, j), 0) + 1
+    assert all(v == 1 for v in seen.values())
+    assert set(seen) == {(s, j) for s in range(len(counts)) for j in range(int(counts[s]))}
+    assert res["frames"] == int(counts.sum()) * 100 and res["secs"] == 2.0
+    # both ranks hold work, and neither holds every scene
+    assert all(0 < len({s for s, _, _ in p.tolist()}) < len(counts) for p in res["parts"])
