@@ -171,6 +171,17 @@ int sim_step(sim_ctx* ctx, int32_t n_agents, float* state, const float* cmd, flo
 int sim_render(sim_ctx* ctx, int32_t n_agents, const int32_t* scene_of_agent, const float* state, float* depth,
                uint8_t* rgb, int32_t* hit_id, void* stream);
 
+/* Load analysis of the context's last sim_render launch (no counterpart in
+ * the paper): the traversal cost of every image tile -- the node and leaf
+ * visits of the warp that rendered it, summed over a split tile's quarters --
+ * which is what the next launch's longest-first order is estimated from.
+ * costs host uint32 [n][tiles_y][tiles_x] (tiles of the context's render
+ * configuration, sim_get_render_config) or NULL to ask for the size only;
+ * *n_items receives n * tiles_y * tiles_x.  Synchronises the device.
+ * Errors: INVALID_ARG (null n_items, or max_items below the size), NOT_FOUND
+ * (no sim_render launch recorded). */
+int sim_render_tile_costs(sim_ctx* ctx, uint32_t* costs, int64_t max_items, int64_t* n_items);
+
 /* As sim_render with every agent in one scene. */
 int sim_render_scene(sim_ctx* ctx, int32_t n_agents, int32_t scene_id, const float* state, float* depth,
                      uint8_t* rgb, int32_t* hit_id, void* stream);

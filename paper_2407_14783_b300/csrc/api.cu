@@ -428,6 +428,9 @@ RenderArgs render_args(sim_ctx* c, int n, const int32_t* soa, const float* state
     a.sched = nullptr;
     a.heavy = nullptr;
     a.done = nullptr;
+    a.acc = nullptr;
+    a.cost = nullptr;
+    a.pose = nullptr;
     a.sched_cap = 0;
     a.launch_id = c->launch_id.fetch_add(1) + 1;
     a.seg = nullptr;
@@ -455,11 +458,12 @@ int check_render_args(sim_ctx* c, int n, const void* soa, const void* state) {
 }
 
 // Scheduling hints: a header (kSchedHeaderWords words), kBuckets item lists of
-// cap entries for each of the two slots, one mark and one quarter accumulator
-// per item.  Zeroed at allocation.
+// cap entries, then per item a done mark, a quarter accumulator and the last
+// launch's cost, and per agent (at most cap agents) the camera attitudes of the
+// last two launches.  Zeroed at allocation.
 size_t sched_bytes_for(int cap) {
-    return sizeof(unsigned long long) * kSchedHeaderWords + 2 * kBuckets * sizeof(unsigned) * (size_t)cap +
-           sizeof(unsigned long long) * cap + sizeof(unsigned) * (size_t)cap;
+    return sizeof(unsigned long long) * kSchedHeaderWords + kBuckets * sizeof(unsigned) * (size_t)cap +
+           sizeof(unsigned long long) * cap + 2 * sizeof(unsigned) * (size_t)cap + 2 * sizeof(float4) * (size_t)cap;
 }
 
 int sched_alloc(sim_ctx* c, int cap, void** mem, cudaStream_t s) {
@@ -474,10 +478,14 @@ void sched_attach(RenderArgs& a, void* mem, int cap) {
     a.sched = (unsigned long long*)p;
     p += sizeof(unsigned long long) * kSchedHeaderWords;
     a.heavy = (unsigned*)p;
-    p += 2 * kBuckets * sizeof(unsigned) * (size_t)cap;
+    p += kBuckets * sizeof(unsigned) * (size_t)cap;
     a.done = (unsigned long long*)p;
     p += sizeof(unsigned long long) * (size_t)cap;
     a.acc = (unsigned*)p;
+    p += sizeof(unsigned) * (size_t)cap;
+    a.cost = (unsigned*)p;
+    p += sizeof(unsigned) * (size_t)cap;
+    a.pose = (float4*)p;
     a.sched_cap = cap;
 }
 
@@ -627,7 +635,21 @@ cudaError_t launch_cfg(const void* kernel, const RenderArgs& a, int warps_per_ct
     const long long need = (items + warps_per_cta - 1) / warps_per_cta;
     if (need < ctas) ctas = (int)std::max(1ll, need);
     void* args[] = {(void*)&a};
-    return cudaLaunchKernel(kernel, dim3(ctas), dim3(32 * warps_per_cta), args, smem, s);
+    if (!a.sched) return cudaLaunchKernel(kernel, dim3(ctas), dim3(32 * warps_per_cta), args, smem, s);
+    // after the schedule's estimate kernel: programmatic dependent launch, so
+    // the ray cast's CTAs start (and prefetch the scenes into L2) while the
+    // estimate runs; the kernel waits for it before reading the schedule
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(32 * warps_per_cta);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, kernel, args);
 }
 }  // namespace vf
 
@@ -912,6 +934,39 @@ int sim_render_ex(sim_ctx* c, int32_t n, const int32_t* soa, const float* state,
     const sim_render_config cfg = c->rcfg;
     if ((rc = ctx_sched(c, render_items(c, n, cfg), s))) return rc;
     return do_render(c, n, soa, state, depth, rgb, hit, false, cfg, s, nullptr, c->sched_mem, c->sched_cap, seg);
+}
+
+int sim_render_tile_costs(sim_ctx* c, uint32_t* costs, int64_t max_items, int64_t* n_items) {
+    if (!c || !n_items) return fail(SIM_ERR_INVALID_ARG, "null argument");
+    *n_items = 0;
+    if (!c->sched_mem) return fail(SIM_ERR_NOT_FOUND, "no render launch recorded yet");
+    DeviceGuard g(c->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    unsigned long long hdr[kSchedHeaderWords];
+    if (e == cudaSuccess) e = cudaMemcpy(hdr, c->sched_mem, sizeof(hdr), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "schedule read-back");
+    const long long total = (long long)hdr[kSchedTotal];
+    const int tiles_x = (int)(hdr[kSchedShape] & 0xFFFFu), tiles_y = (int)((hdr[kSchedShape] >> 16) & 0xFFFFu);
+    const long long n = (long long)(hdr[kSchedShape] >> 32);
+    if (total <= 0 || total > c->sched_cap || total != n * tiles_x * tiles_y)
+        return fail(SIM_ERR_NOT_FOUND, "no render launch recorded yet");
+    *n_items = total;
+    if (!costs) return SIM_OK;
+    if (max_items < total) return fail(SIM_ERR_INVALID_ARG, "cost buffer smaller than the launch's tile count");
+    RenderArgs a{};
+    sched_attach(a, c->sched_mem, c->sched_cap);
+    std::vector<uint32_t> by_item((size_t)total);
+    e = cudaMemcpy(by_item.data(), a.cost, sizeof(uint32_t) * (size_t)total, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "schedule read-back");
+    // item = (rank row * tiles_x + tx) * n + agent; rank rows run from the image centre outwards
+    const int mid = tiles_y >> 1;
+    for (int rr = 0; rr < tiles_y; ++rr) {
+        const int ty = (rr & 1) ? mid - 1 - (rr >> 1) : mid + (rr >> 1);
+        for (int tx = 0; tx < tiles_x; ++tx)
+            for (long long ag = 0; ag < n; ++ag)
+                costs[(ag * tiles_y + ty) * tiles_x + tx] = by_item[(size_t)(((long long)rr * tiles_x + tx) * n + ag)];
+    }
+    return SIM_OK;
 }
 
 int sim_render(sim_ctx* c, int32_t n, const int32_t* soa, const float* state, float* depth, uint8_t* rgb,

@@ -48,10 +48,15 @@ cudaError_t lbvh_build(int64_t nt, const float* d_verts, const int* d_tris, cons
                        LbvhAlloc alloc, void* alloc_user, LbvhResult* out, cudaStream_t s);
 
 // raycast.cu
-constexpr int kBuckets = 4;       // cost buckets of the longest-first schedule
+// Cost buckets of the longest-first schedule: estimates over 4, 2, 1.25, 0.8,
+// 0.5 and 0.25 times the mean cost, and the rest.  The first kHeavyBuckets are
+// the heavy ones that a streamed launch interleaves with the natural order.
+constexpr int kBuckets = 7;
+constexpr int kHeavyBuckets = 4;
 constexpr int kSchedEpoch = 2;    // header words of the scheduling state
 constexpr int kSchedTotal = 3;
-constexpr int kSchedLen = 4;      // kSchedLen .. kSchedLen + 2 * kBuckets - 1
+constexpr int kSchedLen = 4;      // kSchedLen .. kSchedLen + kBuckets - 1
+constexpr int kSchedShape = kSchedLen + kBuckets;
 constexpr int kSchedHeaderWords = 16;
 
 struct RenderArgs {
@@ -69,16 +74,21 @@ struct RenderArgs {
     int* err;
     long long* counters; // traversal counters (COUNT builds)
     // Longest-first scheduling state carried between launches (may be null):
-    // sched[0..1] cost sums of the two slots, sched[kSchedEpoch] epoch (its low
-    // bit is this launch's read slot), sched[kSchedTotal] item count of the
-    // launch that filed the buckets, sched[kSchedLen + slot * kBuckets + b]
-    // bucket lengths; heavy[slot][b][cap] the bucket lists; done[cap] marks of
-    // items already rendered in this launch; acc[cap] cost sums and arrival
-    // counts of split tiles' quarters (zero between launches).
+    // sched[e & 1] the cost sum of the launch with epoch e, sched[kSchedEpoch]
+    // the epoch, sched[kSchedTotal] / sched[kSchedShape] item count and (tiles
+    // x, tiles y, agents) of the last completed launch, sched[kSchedLen + b]
+    // the lengths of this launch's buckets; heavy[b][cap] the bucket lists
+    // (filed by sched_estimate_kernel just before the launch); done[cap] marks
+    // of items already rendered in this launch; acc[cap] cost sums and arrival
+    // counts of split tiles' quarters (zero between launches); cost[cap] each
+    // item's cost in the last launch; pose[2][cap] each agent's unit attitude
+    // quaternion at the launch with epoch e in slot e & 1.
     unsigned long long* sched;
     unsigned* heavy;
     unsigned long long* done;
     unsigned* acc;
+    unsigned* cost;
+    float4* pose;
     int sched_cap;
     unsigned launch_id;  // distinct per host-side launch
     int32_t* seg;        // segmentation image [n][H][W] or null

@@ -193,6 +193,149 @@ __device__ __forceinline__ void tile_bounds(const float flo[3], const float fhi[
 
 __device__ __forceinline__ float comp4(const float4& v, int s) { return s == 0 ? v.x : s == 1 ? v.y : s == 2 ? v.z : v.w; }
 
+// Identity of a launch's item layout: item ids are (rank * n + agent), so the
+// costs of one launch describe the next only when both agree on all three.
+__host__ __device__ __forceinline__ unsigned long long sched_shape(int tiles_x, int tiles_y, int n) {
+    return (unsigned long long)tiles_x | ((unsigned long long)tiles_y << 16) | ((unsigned long long)(unsigned)n << 32);
+}
+
+// Tile rows are ranked from the image centre outwards (rank row 0 is row
+// tiles_y / 2, then the rows above and below it in turn): tile row of a rank
+// row, and back.
+__device__ __forceinline__ int tile_row_of(int rr, int tiles_y) {
+    const int mid = tiles_y >> 1;
+    return (rr & 1) ? mid - 1 - (rr >> 1) : mid + (rr >> 1);
+}
+__device__ __forceinline__ int rank_row_of(int ty, int tiles_y) {
+    const int mid = tiles_y >> 1;
+    return ty >= mid ? 2 * (ty - mid) : 2 * (mid - 1 - ty) + 1;
+}
+
+__device__ __forceinline__ void quat_rotation(float w, float x, float y, float z, float R[3][3]) {
+    R[0][0] = w * w + x * x - y * y - z * z;
+    R[0][1] = 2.0f * (x * y - w * z);
+    R[0][2] = 2.0f * (x * z + w * y);
+    R[1][0] = 2.0f * (x * y + w * z);
+    R[1][1] = w * w - x * x + y * y - z * z;
+    R[1][2] = 2.0f * (y * z - w * x);
+    R[2][0] = 2.0f * (x * z - w * y);
+    R[2][1] = 2.0f * (y * z + w * x);
+    R[2][2] = w * w - x * x - y * y + z * z;
+}
+
+// Files the coming launch's work items into the cost buckets, one thread per
+// tile (a warp holds 32 tiles of one agent when the agent has that many).  A
+// tile's estimate is the previous launch's cost of the image region its rays
+// looked at then: the tile's centre direction is carried from the agent's
+// current camera attitude into the previous one (in one control step an agent
+// turns by up to a few pixels but moves a centimetre or so, so the rotation
+// alone moves the image), and the previous tiles that the moved tile overlaps
+// contribute by overlap area; parts outside the previous image count at the
+// mean cost.  The launch's order only changes which warp renders which tile
+// when, never a pixel's value.
+__global__ void __launch_bounds__(256) sched_estimate_kernel(RenderArgs A, int TW, int TH) {
+    // the ray cast that follows may start its prologue now; everything this
+    // kernel reads was written by earlier stream work, so wait for it first
+    // (every thread, before any early exit: the ray cast's own wait relies on
+    // this kernel finishing only after that work)
+    asm volatile("griddepcontrol.launch_dependents;");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int lane = threadIdx.x & 31;
+    const int n = A.n_agents;
+    const int W = A.cam.W, H = A.cam.H;
+    const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH, tiles = tiles_x * tiles_y;
+    const long long total = (long long)n * tiles;
+    if (total > A.sched_cap) return;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // agent-major: t = agent * tiles + p
+    const bool act = t < total;
+    const int agent = act ? (int)(t / tiles) : 0, p = act ? (int)(t - (long long)agent * tiles) : 0;
+    unsigned long long* S = A.sched;
+    const unsigned long long ep = S[kSchedEpoch];
+    const bool valid = S[kSchedTotal] == (unsigned long long)total && S[kSchedShape] == sched_shape(tiles_x, tiles_y, n);
+    const float mean = valid ? (float)S[(ep + 1) & 1] / (float)total : 0.0f;
+    int b = -1;
+    unsigned item = 0;
+    if (act) {
+        const float* st = A.state;
+        float qw = __ldg(st + 6 * n + agent), qx = __ldg(st + 7 * n + agent), qy = __ldg(st + 8 * n + agent),
+              qz = __ldg(st + 9 * n + agent);
+        const float q2 = qw * qw + qx * qx + qy * qy + qz * qz;
+        const float qi = q2 > 0.0f ? rsqrtf(q2) : 0.0f;
+        qw *= qi;
+        qx *= qi;
+        qy *= qi;
+        qz *= qi;
+        const int tx = p % tiles_x, ty = p / tiles_x;
+        item = (unsigned)((long long)(rank_row_of(ty, tiles_y) * tiles_x + tx) * n + agent);
+        // attitudes are double-buffered by epoch: this launch reads the
+        // previous launch's slot and records its own in the other
+        if (p == 0) A.pose[(size_t)(ep & 1) * A.sched_cap + agent] = make_float4(qw, qx, qy, qz);
+        if (mean > 0.0f && q2 > 0.0f) {
+            const float4 qo = A.pose[(size_t)((ep + 1) & 1) * A.sched_cap + agent];
+            float Rn[3][3], Ro[3][3];
+            quat_rotation(qw, qx, qy, qz, Rn);
+            quat_rotation(qo.x, qo.y, qo.z, qo.w, Ro);
+            const float pix = A.cam.pix, area = (float)(TW * TH);
+            // tile centre in continuous pixel coordinates, its body-frame direction
+            const float u = (tx + 0.5f) * TW, v = (ty + 0.5f) * TH;
+            const float d[3] = {1.0f, -(2.0f * u - W) * 0.5f * pix, -(2.0f * v - H) * 0.5f * pix};
+            // world direction, then the previous body frame's
+            float w[3], e[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) w[i] = Rn[i][0] * d[0] + Rn[i][1] * d[1] + Rn[i][2] * d[2];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) e[i] = Ro[0][i] * w[0] + Ro[1][i] * w[1] + Ro[2][i] * w[2];
+            float est = mean;
+            if (e[0] > 1e-3f) {
+                // the moved tile's corner in the previous image
+                const float x0 = 0.5f * W - e[1] / (e[0] * pix) - 0.5f * TW;
+                const float y0 = 0.5f * H - e[2] / (e[0] * pix) - 0.5f * TH;
+                if (fabsf(x0) < 4.0f * W && fabsf(y0) < 4.0f * H) {
+                    const int ox0 = (int)floorf(x0 / TW), oy0 = (int)floorf(y0 / TH);
+                    float acc = 0.0f, cov = 0.0f;
+#pragma unroll
+                    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                        for (int dx = 0; dx < 2; ++dx) {
+                            const int ox = ox0 + dx, oy = oy0 + dy;
+                            if (ox < 0 || oy < 0 || ox >= tiles_x || oy >= tiles_y) continue;
+                            const float wx = fminf(x0 + TW, (float)((ox + 1) * TW)) - fmaxf(x0, (float)(ox * TW));
+                            const float wy = fminf(y0 + TH, (float)((oy + 1) * TH)) - fmaxf(y0, (float)(oy * TH));
+                            if (wx <= 0.0f || wy <= 0.0f) continue;
+                            const long long it = (long long)(rank_row_of(oy, tiles_y) * tiles_x + ox) * n + agent;
+                            acc += wx * wy * (float)A.cost[it];
+                            cov += wx * wy;
+                        }
+                    est = (acc + fmaxf(area - cov, 0.0f) * mean) / area;
+                }
+            }
+            b = est > 4.0f * mean    ? 0
+                : est > 2.0f * mean  ? 1
+                : est > 1.25f * mean ? 2
+                : est > 0.8f * mean  ? 3
+                : est > 0.5f * mean  ? 4
+                : est > 0.25f * mean ? 5
+                                     : 6;
+        }
+    }
+    // warp-aggregated filing: lane k reserves the warp's slots in bucket k,
+    // all buckets' atomics in flight at once
+    unsigned mine = 0u, cnt_k = 0u;
+#pragma unroll
+    for (int k = 0; k < kBuckets; ++k) {
+        const unsigned m = __ballot_sync(kFull, b == k);
+        if (b == k) mine = m;
+        if (lane == k) cnt_k = (unsigned)__popc(m);
+    }
+    unsigned long long base = 0;
+    if (lane < kBuckets && cnt_k > 0) base = atomicAdd(&S[kSchedLen + lane], (unsigned long long)cnt_k);
+    const unsigned long long my_base = __shfl_sync(kFull, base, b < 0 ? 0 : b);
+    if (b >= 0) {
+        const unsigned long long slot = my_base + (unsigned long long)__popc(mine & ((1u << lane) - 1u));
+        if (slot < (unsigned long long)A.sched_cap) A.heavy[(size_t)b * A.sched_cap + slot] = item;
+    }
+}
+
 template <int TW, int TH, int RPL, bool SMEM_STACK, bool STAGE, bool COUNT, bool WIDE, int EXTRA>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6) raycast_kernel(RenderArgs A) {
     static_assert(TW * TH == 32 * RPL, "tile must hold 32 * RPL pixels");
@@ -210,7 +353,6 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
     // COUNT statistics: per work item (warp) and per ray (what each ray's own walk needs)
     long long c_nodes = 0, c_tris = 0, c_large = 0, c_items = 0, c_need_nodes = 0, c_need_tris = 0;
 
-    const unsigned long long noise_frame = A.noise.enabled ? *A.noise_frame : 0ull;
     if (A.prefetch_l2) {
         // After an L2 flush the first walks would pay DRAM latency on every node of
         // their dependent chains; the whole grid streams the scenes into L2 at
@@ -229,14 +371,22 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                     asm volatile("prefetch.global.L2 [%0];" ::"l"(bases[k] + off));
         }
     }
-    // Longest-first order from the previous launch with the same item count:
-    // its tiles were filed into cost buckets (over 4, 2, 1.25 and 0.8 times the
-    // mean cost); this launch hands out bucket 0 first, each tile as kSplit
-    // quarter-tile sub-packets on separate warps (a quarter walks only its own
-    // rays' paths, which shortens the longest dependent chain of node fetches),
-    // then buckets 1-3 whole, then every tile not yet rendered in natural order
-    // (edge rows first when the buckets hold entries, centre rows first when
-    // they are empty).
+    // launched as a programmatic dependent of the estimate kernel when
+    // scheduled: the prefetch above overlaps it, nothing produced by earlier
+    // stream work is read before this point
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const unsigned long long noise_frame = A.noise.enabled ? *A.noise_frame : 0ull;
+    // Longest-first order: sched_estimate_kernel, launched just before, filed
+    // every tile of this launch into a cost bucket (kBuckets) by the previous
+    // launch's tile costs moved to the current camera poses; this launch hands
+    // out bucket 0 first, each tile as kSplit quarter-tile sub-packets on
+    // separate warps (a quarter walks only its own rays' paths, which shortens
+    // the longest dependent chain of node fetches), then the other buckets
+    // whole, costliest first.  A last sweep renders whatever no bucket held
+    // (entries of a concurrent launch sharing the buffers, or no estimate at
+    // all): by chunks of 32 items checked against this launch's done marks
+    // when the buckets held every item, else item by item in natural order
+    // (centre rows first without hints, edge rows first with partial ones).
     const bool sched = A.sched != nullptr && total <= A.sched_cap;
     // A launch that streams its bands to the host interleaves buckets 1-3 with
     // natural-order items one for one: a band is complete only when all its
@@ -248,85 +398,104 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
     // to matter: at most 12 tiles per resident warp.
     const bool allow_split = total <= 12ll * gridDim.x * kWarpsPerCta;
     __shared__ long long s_end[kBuckets];  // cumulative ends of the buckets in the counter's range
-    __shared__ float s_mean;
+    __shared__ long long s_entries;        // bucket entries (a split tile counts once)
     unsigned long long mark = 0;
-    int rd = 0;
+    unsigned ep = 0;
     if (sched) {
-        const unsigned ep = (unsigned)A.sched[kSchedEpoch];
-        rd = ep & 1;
+        ep = (unsigned)A.sched[kSchedEpoch];
         mark = ((unsigned long long)A.launch_id << 32) | ep;
         if (threadIdx.x == 0) {
-            const bool valid = (long long)A.sched[kSchedTotal] == total;
-            long long end = 0;
+            long long end = 0, entries = 0;
             for (int b = 0; b < kBuckets; ++b) {
-                const long long len = valid ? (long long)min(A.sched[kSchedLen + rd * kBuckets + b],
-                                                            (unsigned long long)total)
-                                            : 0ll;
+                const long long len = (long long)min(A.sched[kSchedLen + b], (unsigned long long)total);
                 end += (b == 0 && allow_split) ? len * kSplit : len;
+                entries += len;
                 s_end[b] = end;
             }
-            s_mean = valid ? (float)A.sched[rd] / (float)total : 0.0f;
+            s_entries = entries;
         }
     } else if (threadIdx.x == 0) {
         for (int b = 0; b < kBuckets; ++b) s_end[b] = 0;
-        s_mean = 0.0f;
+        s_entries = 0;
     }
     __syncthreads();
-    const float mean = s_mean;
     const bool hinted = s_end[kBuckets - 1] > 0;
+    // the buckets held as many entries as the launch has items: the sweep only
+    // checks done marks, 32 items per claim
+    const bool sweep = !weave && s_entries >= total;
+    unsigned pend = 0u;  // sweep: items of the warp's chunk that are still to render
+    long long pend_base = 0;
     for (;;) {
         long long item = 0;
         int sub = -1;
-        if (lane == 0) {
-            const long long k = (long long)atomicAdd(A.counter, 1u);
-            // position in the bucket lists, or -1 for a natural-order item at nat
-            long long kb = -1, nat = 0;
-            if (!weave) {
-                if (k < s_end[kBuckets - 1]) kb = k;
-                else nat = k - s_end[kBuckets - 1];
-            } else if (k < s_end[0]) {
-                kb = k;
-            } else {
-                const long long r = k - s_end[0], pair = s_end[kBuckets - 1] - s_end[0];
-                if (r < 2 * pair) {
-                    if (r & 1) nat = r >> 1;
-                    else kb = s_end[0] + (r >> 1);
+        long long chunk = -1;
+        if (pend) {
+            item = pend_base + (__ffs(pend) - 1);
+            pend &= pend - 1;
+        } else {
+            if (lane == 0) {
+                const long long k = (long long)atomicAdd(A.counter, 1u);
+                // position in the bucket lists, or -1 for a natural-order item at nat
+                long long kb = -1, nat = 0;
+                if (!weave) {
+                    if (k < s_end[kBuckets - 1]) kb = k;
+                    else nat = k - s_end[kBuckets - 1];
+                } else if (k < s_end[0]) {
+                    kb = k;
                 } else {
-                    nat = r - pair;
+                    // a streamed launch interleaves the heavy buckets 1.. with the
+                    // natural order, which also covers the cheap buckets' tiles
+                    const long long r = k - s_end[0], pair = s_end[kHeavyBuckets - 1] - s_end[0];
+                    if (r < 2 * pair) {
+                        if (r & 1) nat = r >> 1;
+                        else kb = s_end[0] + (r >> 1);
+                    } else {
+                        nat = r - pair;
+                    }
+                }
+                if (kb < 0 && sweep) {
+                    chunk = nat;
+                } else if (kb >= 0) {
+                    int b = 0;
+                    while (kb >= s_end[b]) ++b;
+                    const long long j = kb - (b == 0 ? 0ll : s_end[b - 1]);
+                    const unsigned* list = A.heavy + (size_t)b * A.sched_cap;
+                    if (b == 0 && allow_split) {
+                        item = list[j / kSplit];
+                        sub = (int)(j % kSplit);
+                    } else {
+                        item = list[j];
+                    }
+                    // an entry from a concurrent launch of another size may not fit this one
+                    if (item >= total) item = -1;
+                    else if (b == 0 || !weave) __stcg(A.done + item, mark);
+                    else if (atomicExch(A.done + item, mark) == mark) item = -1;  // taken in natural order
+                } else {
+                    // with hints the natural phase holds only tiles the last launch
+                    // found cheap, and taking the edge rows first measured faster
+                    // (0.8% with moving poses at 4x8 tiles); without hints the
+                    // centre rows, where most costly tiles lie, go first
+                    item = (hinted && !weave && nat < total) ? total - 1 - nat : nat;
+                    if (item >= total) {
+                        item = total;  // no work left
+                    } else if (weave) {
+                        if (atomicExch(A.done + item, mark) == mark) item = -1;  // taken from a bucket
+                    } else if (sched && __ldcg(A.done + item) == mark) {
+                        item = -1;  // done from a bucket
+                    }
                 }
             }
-            if (kb >= 0) {
-                int b = 0;
-                while (kb >= s_end[b]) ++b;
-                const long long j = kb - (b == 0 ? 0ll : s_end[b - 1]);
-                const unsigned* list = A.heavy + ((size_t)rd * kBuckets + b) * A.sched_cap;
-                if (b == 0 && allow_split) {
-                    item = list[j / kSplit];
-                    sub = (int)(j % kSplit);
-                } else {
-                    item = list[j];
-                }
-                // an entry from a concurrent launch of another size may not fit this one
-                if (item >= total) item = -1;
-                else if (b == 0 || !weave) __stcg(A.done + item, mark);
-                else if (atomicExch(A.done + item, mark) == mark) item = -1;  // taken in natural order
-            } else {
-                // with hints the natural phase holds only tiles the last launch
-                // found cheap, and taking the edge rows first measured faster
-                // (0.8% with moving poses at 4x8 tiles); without hints the
-                // centre rows, where most costly tiles lie, go first
-                item = (hinted && !weave && nat < total) ? total - 1 - nat : nat;
-                if (item >= total) {
-                    item = total;  // no work left
-                } else if (weave) {
-                    if (atomicExch(A.done + item, mark) == mark) item = -1;  // taken from a bucket
-                } else if (sched && __ldcg(A.done + item) == mark) {
-                    item = -1;  // done from a bucket
-                }
+            item = __shfl_sync(kFull, item, 0);
+            sub = __shfl_sync(kFull, sub, 0);
+            chunk = __shfl_sync(kFull, chunk, 0);
+            if (chunk >= 0) {
+                if (chunk * 32 >= total) break;
+                const long long it = chunk * 32 + lane;
+                pend = __ballot_sync(kFull, it < total && __ldcg(A.done + it) != mark);
+                pend_base = chunk * 32;
+                continue;
             }
         }
-        item = __shfl_sync(kFull, item, 0);
-        sub = __shfl_sync(kFull, sub, 0);
         if (item < 0) continue;
         if (item >= total) break;
         // after a device-detected fault every warp stops taking work
@@ -337,8 +506,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
         // ones.
         const int rank = (int)(item / A.n_agents);
         const int agent = (int)(item - (long long)rank * A.n_agents);
-        const int rrow = rank / tiles_x, mid = tiles_y >> 1;
-        const int ty = (rrow & 1) ? mid - 1 - (rrow >> 1) : mid + (rrow >> 1);
+        const int ty = tile_row_of(rank / tiles_x, tiles_y);
         const int tx0 = (rank % tiles_x) * TW, ty0 = ty * TH;
         const int sid = __ldg(A.scene_of_agent + agent);
         const bool scene_ok = sid >= 0 && sid < A.n_scenes && A.table[sid].live;
@@ -763,30 +931,17 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
         }
         if (COUNT) ++c_items;
         if (sched && lane == 0) {
-            // file this tile for the next launch by its cost; a split tile is
-            // judged by the sum of its quarters, by the quarter that completes it
-            const int wr = rd ^ 1;
-            atomicAdd(&A.sched[wr], (unsigned long long)item_cost);
-            unsigned est = 0;
-            bool judge = false;
+            // record this tile's cost for the next launch's schedule; a split
+            // tile's cost is the sum of its quarters, recorded by the quarter
+            // that completes it
+            atomicAdd(&A.sched[ep & 1], (unsigned long long)item_cost);
             if (sub < 0) {
-                est = (unsigned)item_cost;
-                judge = true;
+                A.cost[item] = (unsigned)item_cost;
             } else {
                 const unsigned old = atomicAdd(A.acc + item, (unsigned)item_cost | (1u << 24));
                 if ((old >> 24) == (unsigned)(kSplit - 1)) {
-                    est = (old & 0xFFFFFFu) + (unsigned)item_cost;
+                    A.cost[item] = (old & 0xFFFFFFu) + (unsigned)item_cost;
                     A.acc[item] = 0u;
-                    judge = true;
-                }
-            }
-            if (judge && mean > 0.0f) {
-                const float e = (float)est;
-                const int b = e > 4.0f * mean ? 0 : e > 2.0f * mean ? 1 : e > 1.25f * mean ? 2 : e > 0.8f * mean ? 3 : -1;
-                if (b >= 0) {
-                    const unsigned long long k = atomicAdd(&A.sched[kSchedLen + wr * kBuckets + b], 1ull);
-                    if (k < (unsigned long long)A.sched_cap)
-                        A.heavy[((size_t)wr * kBuckets + b) * A.sched_cap + k] = (unsigned)item;
                 }
             }
         }
@@ -818,11 +973,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
             *A.done_ctas = 0u;
             if (A.noise.enabled) *A.noise_frame = noise_frame + 1ull;
             if (sched) {
-                // this launch's read slot becomes the next launch's write slot
-                A.sched[rd] = 0ull;
-                for (int b = 0; b < kBuckets; ++b) A.sched[kSchedLen + rd * kBuckets + b] = 0ull;
+                // the next launch sums its costs into the other slot; its
+                // buckets are filed afresh by its own estimate
+                A.sched[(ep + 1) & 1] = 0ull;
+                for (int b = 0; b < kBuckets; ++b) A.sched[kSchedLen + b] = 0ull;
                 A.sched[kSchedTotal] = (unsigned long long)total;
-                A.sched[kSchedEpoch] = A.sched[kSchedEpoch] + 1ull;
+                A.sched[kSchedShape] = sched_shape(tiles_x, tiles_y, A.n_agents);
+                A.sched[kSchedEpoch] = (unsigned long long)ep + 1ull;
             }
             __threadfence();
         }
@@ -913,6 +1070,23 @@ bool render_config_valid(const sim_render_config& c) {
 }
 
 cudaError_t launch_render(const RenderArgs& a, const sim_render_config& c, int ctas, bool count, cudaStream_t s) {
+    if (a.sched && a.n_agents > 0 && c.tile_w > 0 && c.tile_h > 0) {
+        const long long items = (long long)a.n_agents * ((a.cam.W + c.tile_w - 1) / c.tile_w) *
+                                ((a.cam.H + c.tile_h - 1) / c.tile_h);
+        // a programmatic dependent of the previous kernel: its launch overlaps
+        // that kernel's tail, and it waits for it before reading anything
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)((items + 255) / 256));
+        cfg.blockDim = dim3(256);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, sched_estimate_kernel, a, c.tile_w, c.tile_h);
+        if (e != cudaSuccess) return e;
+    }
     return count ? dispatch<true>(a, c, ctas, s) : dispatch<false>(a, c, ctas, s);
 }
 

@@ -198,6 +198,18 @@ class Sim:
         B.check(rc, "sim_render", self.h)
         return depth, rgb, hit
 
+    def tile_costs(self) -> np.ndarray:
+        """Traversal cost of every tile of the last sim_render launch:
+        uint32 [n, tiles_y, tiles_x] (see sim_render_tile_costs)."""
+        k = ctypes.c_int64()
+        B.check(self.L.sim_render_tile_costs(self.h, None, 0, ctypes.byref(k)), "sim_render_tile_costs", self.h)
+        out = np.zeros(k.value, np.uint32)
+        B.check(self.L.sim_render_tile_costs(self.h, out.ctypes.data_as(ctypes.c_void_p), k.value, ctypes.byref(k)),
+                "sim_render_tile_costs", self.h)
+        cfg = self.render_config()
+        tx, ty = -(-self.W // cfg["tile_w"]), -(-self.H // cfg["tile_h"])
+        return out.reshape(-1, ty, tx)
+
     def nearest_obstacle(self, scene_of_agent, state, max_dist: float = 10.0, stream=None):
         """Closest mesh point of every agent: (dist [n], point [3, n], tri [n])."""
         n = state.shape[1]

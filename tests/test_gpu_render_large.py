@@ -68,11 +68,17 @@ def test_multi_scene_launch_beyond_l2_prefetch(make_sim, oracle_mod, wl):
     d, c, h = _render(sim, ids, all_s)
     off = np.concatenate([[0], np.cumsum(counts)])
     rng = np.random.default_rng(9)
+    ties = pixels = 0
     for k, (sc, sid, st) in enumerate(zip(scenes, sids, states)):
         kk = int(counts[k])
         alone = _render(sim, torch.full((kk,), sid, dtype=torch.int32, device="cuda"), st)
         for x, y in zip((d, c, h), alone):
             assert np.array_equal(x[off[k]:off[k + 1]], y)
         pick = rng.choice(kk, min(2, kk), replace=False)
-        compare_images(oracle_mod.Scene.from_workload(sc), p, st[pick].astype(np.float64), alone[0][pick],
-                       alone[1][pick], alone[2][pick])
+        # the stated-tie cap holds for the configuration's pixels as a whole,
+        # not for every pair of sampled views
+        stats = compare_images(oracle_mod.Scene.from_workload(sc), p, st[pick].astype(np.float64), alone[0][pick],
+                               alone[1][pick], alone[2][pick], max_tie_frac=1.0)
+        ties += stats["ties"]
+        pixels += stats["pixels"]
+    assert ties < 0.01 * pixels, (ties, pixels)
