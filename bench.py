@@ -395,7 +395,7 @@ def run_ours(args):
         best = sim.render_config()
     else:
         best, times = sim.autotune(ids, state, depth, rgb, iters=3)
-        tune = {"{tile_w}x{tile_h}/rpl{rays_per_lane}/{s}stack/{g}/bvh{node_width}".format(
+        tune = {"{tile_w}x{tile_h}/rpl{rays_per_lane}/{s}stack{stack_depth}/{g}/bvh{node_width}".format(
                     s="smem" if c["stack_in_smem"] else "reg", g="staged" if c["stage_in_smem"] else "bcast", **c):
                 round(t, 4) for c, t in zip(Sim.render_configs(), times)}
     for t in range(W):
@@ -546,7 +546,8 @@ def run_ours(args):
             "config": {"workload": "single large scene: 208,812 triangles, 256 agents per GPU, RK4 dt=0.02, "
                                    "64x64 FP32 depth + uint8 RGB", "agents_per_gpu": n,
                        "triangles": int(scene.n_tris), "l2": "flushed between timed steps (256 MiB write)",
-                       "reset_every_steps": EPISODE, "render_config": best, "autotune_ms": tune},
+                       "reset_every_steps": EPISODE, "render_config": best, "autotune_ms": tune,
+                       "bvh_depth": sim.scene_info(sid)["depth"]},
             "e2e": e2e, "gpu_launches": 2 * K,
             "breakdown_ms": {"dynamics": statistics.mean(dyn_ms), "render": render_ms,
                              "from": "a separate pass of %d steps with an event between the two" % len(evb)},
@@ -875,20 +876,16 @@ def run_diff(args):
     return 0
 
 
-def run_swarm(args):
-    """Multi-agent mode (Sec. III-B): 256 agents flying in 64 formations of 4
-    (1.5 m square, common heading) through the 208,812-triangle scene, all one
-    swarm, so each camera also sees the other drones.  One step = dynamics +
-    swarm render + pairwise proximity (collision query).  Reports agent-frames/s
-    and the same loop in the parallel-agents mode beside it."""
+def swarm_case(p, scene, n_form, steps, warmup, per=4, seed=71):
+    """n_form formations of `per` drones (1.5 m square, common heading) flying
+    through the scene as one swarm.  Returns (ms per step with the drones
+    visible + proximity, ms per step in the parallel-agents mode, drone pixel
+    fraction)."""
     import torch
     from paper_2407_14783_b300.sim import Sim, to_soa
-    p = wl.params()
     w_h, u_h = _hover(p)
-    scene = wl.cluttered_scene(seed=2)
-    n_form, per = 64, 4
     n = n_form * per
-    lead = wl.spawn_states(scene, n_form, 71, w_h)
+    lead = wl.spawn_states(scene, n_form, seed, w_h)
     s0 = np.repeat(lead, per, axis=0)
     offs = np.array([[0.75, 0.75], [0.75, -0.75], [-0.75, 0.75], [-0.75, -0.75]])
     for f in range(n_form):
@@ -898,8 +895,8 @@ def run_swarm(args):
             s0[f * per + k, 0] += c * offs[k, 0] - sn * offs[k, 1]
             s0[f * per + k, 1] += sn * offs[k, 0] + c * offs[k, 1]
     s0 = s0.astype(np.float32)
-    T = args.warmup + args.steps
-    U = wl.hover_commands(T, n, 72, u_h, rate_range=0.3).astype(np.float32)
+    T = warmup + steps
+    U = wl.hover_commands(T, n, seed + 1, u_h, rate_range=0.3).astype(np.float32)
     sim = Sim(p)
     sid = sim.add_workload_scene(scene)
     ids = torch.full((n,), sid, dtype=torch.int32, device="cuda")
@@ -925,7 +922,7 @@ def run_swarm(args):
             if swarm:
                 sim.swarm_proximity(ids, state, radius)
             e1.record(stream)
-            if t >= args.warmup:
+            if t >= warmup:
                 times.append((e0, e1))
         torch.cuda.synchronize()
         sim.check()
@@ -934,6 +931,28 @@ def run_swarm(args):
     ms_swarm = loop(True)
     drone_px = float((h < -1).float().mean().item())
     ms_plain = loop(False)
+    sim.close()
+    return ms_swarm, ms_plain, drone_px
+
+
+def run_swarm(args):
+    """Multi-agent mode (Sec. III-B): 256 agents flying in 64 formations of 4
+    (1.5 m square, common heading) through the 208,812-triangle scene, all one
+    swarm, so each camera also sees the other drones.  One step = dynamics +
+    swarm render + pairwise proximity (collision query).  Reports agent-frames/s
+    and the same loop in the parallel-agents mode beside it, and the same for
+    swarms of 1,024 and 4,096 drones in the scene (the per-tile cull passes over
+    every member of the swarm, so its cost grows with the swarm)."""
+    p = wl.params()
+    scene = wl.cluttered_scene(seed=2)
+    half, radius = (0.25, 0.25, 0.06), 0.3
+    ms_swarm, ms_plain, drone_px = swarm_case(p, scene, 64, args.steps, args.warmup)
+    sweep = {}
+    for n_form in (256, 1024):
+        a, b, px = swarm_case(p, scene, n_form, args.steps, args.warmup)
+        sweep[str(4 * n_form)] = {"swarm_ms_per_step": a, "parallel_ms_per_step": b, "swarm_over_parallel_time": a / b,
+                                  "agent_frames_per_s": 4 * n_form / (a * 1e-3), "drone_pixel_fraction": px}
+    n = 256
     line = {"metric": "agent-frames/s (dynamics+64x64 depth/RGB, multi-agent mode) on 1 B300",
             "value": n / (ms_swarm * 1e-3), "unit": "agent-frames/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_swarm, "higher_is_better": True, "scaling": "weak",
@@ -944,9 +963,9 @@ def run_swarm(args):
                        "drone_pixel_fraction": drone_px, "parallel_mode_ms_per_step": ms_plain,
                        "swarm_over_parallel_time": ms_swarm / ms_plain,
                        "l2": "flushed between timed steps (256 MiB write)"},
+            "swarm_sizes": sweep,
             "gpu_launches": 7 * args.steps}
     print(json.dumps(line), flush=True)
-    sim.close()
     return 0
 
 

@@ -438,8 +438,11 @@ int sim_server_destroy(sim_server* srv);
 /* Ray-cast kernel configuration (the autotuner's search space).
  *   tile_w x tile_h pixels per warp work item, rays_per_lane in {1, 2}
  *   (tile_w * tile_h = 32 * rays_per_lane); stack_in_smem (1: per-warp stack in
- *   shared memory, 0: stack spread over the warp's registers); stack_depth must
- *   be 64; warps_per_cta must be 4; ctas_per_sm (persistent grid =
+ *   shared memory, 0: stack spread over the warp's registers); stack_depth, the
+ *   traversal stack's entries: 32 or 64 in registers (one or two registers a
+ *   lane), 32, 48 or 64 in shared memory, 64 with 4-wide nodes -- a scene whose
+ *   BVH is as deep as the stack is refused (INVALID_ARG), and the autotuner
+ *   skips such configurations; warps_per_cta must be 4; ctas_per_sm (persistent grid =
  *   ctas_per_sm * SM count; 0 = as many as fit); stage_in_smem (1: node and
  *   triangle records are fetched by a few lanes with coalesced float4 loads
  *   into shared memory and read back by all lanes; 0: every lane loads the
@@ -454,7 +457,9 @@ int sim_set_render_config(sim_ctx* ctx, const sim_render_config* cfg);
 /* Time every supported configuration on the given workload (each `iters`
  * launches, CUDA events on `stream`), select the fastest and return it in
  * *best.  times_ms (may be NULL) receives up to max_times per-config averages
- * in the order of sim_render_config_list.  Synchronises `stream`. */
+ * in the order of sim_render_config_list; a configuration whose stack is too
+ * shallow for the context's deepest scene is not timed and keeps its entry.
+ * Synchronises `stream`. */
 int sim_autotune_render(sim_ctx* ctx, int32_t n_agents, const int32_t* scene_of_agent, const float* state,
                         float* depth, uint8_t* rgb, int32_t iters, sim_render_config* best, float* times_ms,
                         int32_t max_times, void* stream);

@@ -91,6 +91,12 @@ def lib():
                                               P(ctypes.c_uint8), P(ctypes.c_int32), P(ctypes.c_uint8)]
             L.oracle_validate_swarm.argtypes = [vp, P(OracleParams), i64, dp, dp, i64, P(ctypes.c_int64),
                                                 P(ctypes.c_int32), P(ctypes.c_float), P(ctypes.c_uint8)]
+            L.oracle_render_swarm_views.argtypes = [vp, P(OracleParams), i64, dp, P(ctypes.c_int64), i64, dp,
+                                                    ctypes.c_int, dp, P(ctypes.c_uint8), dp, P(ctypes.c_uint8),
+                                                    P(ctypes.c_int32), P(ctypes.c_uint8)]
+            L.oracle_validate_swarm_views.argtypes = [vp, P(OracleParams), i64, dp, P(ctypes.c_int64), i64, dp, dp,
+                                                      i64, P(ctypes.c_int64), P(ctypes.c_int32), P(ctypes.c_float),
+                                                      P(ctypes.c_uint8)]
             L.oracle_swarm_proximity.argtypes = [i64, dp, ctypes.c_double, dp, P(ctypes.c_int32), P(ctypes.c_int32)]
             L.oracle_num_threads.restype = ctypes.c_int
             L.oracle_nearest.argtypes = [vp, i64, dp, ctypes.c_double, dp, dp, P(ctypes.c_int32)]
@@ -201,7 +207,10 @@ class Scene:
         """Returns dict depth [n,H,W] f64, rgb [n,H,W,3] u8, id [n,H,W] i32, tie [n,H,W] bool.
 
         swarm = {"half": (hx, hy, hz), "rgb": (r, g, b)} renders the n agents as
-        one swarm: each sees the other drones (id -2 - j for drone j)."""
+        one swarm: each sees the other drones (id -2 - j for drone j).  With
+        swarm["states"] ([m, 17], the whole swarm) and swarm["self"] ([n], the
+        swarm index of each rendered agent) only the n given cameras are
+        rendered, each seeing every other drone of the swarm."""
         states = _f64(states)
         n = states.shape[0]
         H, W = int(p["height"]), int(p["width"])
@@ -214,6 +223,17 @@ class Scene:
             rc = lib().oracle_render(self.handle, ctypes.byref(make_params(p)), n, _ptr(states, ctypes.c_double),
                                      1 if ub else 0, _ptr(depth, ctypes.c_double), _ptr(rgb, ctypes.c_uint8),
                                      _ptr(hid, ctypes.c_int32), _ptr(tie, ctypes.c_uint8))
+        elif "states" in swarm:
+            half = np.ascontiguousarray(swarm["half"], dtype=np.float64)
+            col = np.ascontiguousarray(swarm.get("rgb", (0, 0, 0)), dtype=np.uint8)
+            allst = _f64(swarm["states"])
+            me = np.ascontiguousarray(swarm["self"], dtype=np.int64)
+            rc = lib().oracle_render_swarm_views(self.handle, ctypes.byref(make_params(p)), n,
+                                                 _ptr(states, ctypes.c_double), _ptr(me, ctypes.c_int64),
+                                                 allst.shape[0], _ptr(allst, ctypes.c_double), 1 if ub else 0,
+                                                 _ptr(half, ctypes.c_double), _ptr(col, ctypes.c_uint8),
+                                                 _ptr(depth, ctypes.c_double), _ptr(rgb, ctypes.c_uint8),
+                                                 _ptr(hid, ctypes.c_int32), _ptr(tie, ctypes.c_uint8))
         else:
             half = np.ascontiguousarray(swarm["half"], dtype=np.float64)
             col = np.ascontiguousarray(swarm.get("rgb", (0, 0, 0)), dtype=np.uint8)
@@ -276,6 +296,16 @@ class Scene:
                                        _ptr(states, ctypes.c_double), pix.shape[0], _ptr(pix, ctypes.c_int64),
                                        _ptr(ids, ctypes.c_int32), _ptr(depth, ctypes.c_float),
                                        _ptr(valid, ctypes.c_uint8))
+        elif "states" in swarm:
+            half = np.ascontiguousarray(swarm["half"], dtype=np.float64)
+            allst = _f64(swarm["states"])
+            me = np.ascontiguousarray(swarm["self"], dtype=np.int64)
+            rc = lib().oracle_validate_swarm_views(self.handle, ctypes.byref(make_params(p)), states.shape[0],
+                                                   _ptr(states, ctypes.c_double), _ptr(me, ctypes.c_int64),
+                                                   allst.shape[0], _ptr(allst, ctypes.c_double),
+                                                   _ptr(half, ctypes.c_double), pix.shape[0],
+                                                   _ptr(pix, ctypes.c_int64), _ptr(ids, ctypes.c_int32),
+                                                   _ptr(depth, ctypes.c_float), _ptr(valid, ctypes.c_uint8))
         else:
             half = np.ascontiguousarray(swarm["half"], dtype=np.float64)
             rc = lib().oracle_validate_swarm(self.handle, ctypes.byref(make_params(p)), states.shape[0],

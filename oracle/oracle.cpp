@@ -666,10 +666,13 @@ inline double t_limit(const OracleParams& p) { return p.max_depth * (1.0 + kTau)
 // delta = kTau * (|o - centre| + |h|), the FP32 error scale of moving the ray
 // into the drone's frame, times the same 50 eps_f32 band as the triangles.
 struct Swarm {
-    const double* states;  // [n][17], the same agents as the render's
+    const double* states;  // [n][17], the swarm's agents
     int64_t n;
     double half[3];
     uint8_t rgb[3];
+    // the swarm index of each rendered view (its own drone is never seen), or
+    // null when the views are the swarm's agents in order
+    const int64_t* self = nullptr;
 };
 
 // Ray (o, d) against the box of half extents h + g (every axis) of the drone
@@ -758,7 +761,7 @@ int render_impl(const OracleScene* s, const OracleParams* p, int64_t n, const do
             double o[3], d[3];
             camera_ray(*p, states + a * 17, r, c, o, d);
             collect_candidates(*s, o, d, t_limit(*p), use_bvh != 0, cands);
-            if (sw) collect_drones(*sw, a, o, d, cands);
+            if (sw) collect_drones(*sw, sw->self ? sw->self[a] : a, o, d, cands);
             const PixelResult pr = classify(cands, p->max_depth);
             if (depth) depth[k] = pr.t;
             if (hit_id) hit_id[k] = output_id(pr.id);
@@ -851,7 +854,7 @@ int validate_impl(const OracleScene* s, const OracleParams* p, int64_t n, const 
             double o[3], d[3];
             camera_ray(*p, states + a * 17, r, c, o, d);
             collect_candidates(*s, o, d, t_limit(*p), use_bvh, cands);
-            if (sw) collect_drones(*sw, a, o, d, cands);
+            if (sw) collect_drones(*sw, sw->self ? sw->self[a] : a, o, d, cands);
             double t_def = std::numeric_limits<double>::infinity();
             for (const Cand& cd : cands)
                 if (cd.h.m > kTau * cd.h.sigma && cd.h.t > kTmin && cd.h.t <= p->max_depth * (1.0 - kTau))
@@ -1069,6 +1072,33 @@ int oracle_validate_swarm(const void* scene, const OracleParams* p, int64_t n, c
     if (!half) return -1;
     Swarm sw{states, n, {half[0], half[1], half[2]}, {0, 0, 0}};
     return validate_impl(static_cast<const OracleScene*>(scene), p, n, states, &sw, npix, pix, id, depth, valid);
+}
+
+// As oracle_render_swarm / oracle_validate_swarm for a chosen set of views:
+// view k has the state views[k] ([n_views][17]) and is agent self[k] of the
+// swarm (swarm [n_swarm][17]), whose other drones it sees.  Lets a test check a
+// few cameras of a large swarm without rendering every camera.
+int oracle_render_swarm_views(const void* scene, const OracleParams* p, int64_t n_views, const double* views,
+                              const int64_t* self, int64_t n_swarm, const double* swarm, int use_bvh,
+                              const double* half, const uint8_t* drone_rgb, double* depth, uint8_t* rgb,
+                              int32_t* hit_id, uint8_t* tie) {
+    if (!half || !drone_rgb || !self || !swarm) return -1;
+    for (int64_t k = 0; k < n_views; ++k)
+        if (self[k] < 0 || self[k] >= n_swarm) return -1;
+    Swarm sw{swarm, n_swarm, {half[0], half[1], half[2]}, {drone_rgb[0], drone_rgb[1], drone_rgb[2]}, self};
+    return render_impl(static_cast<const OracleScene*>(scene), p, n_views, views, use_bvh, &sw, depth, rgb, hit_id,
+                       tie);
+}
+
+int oracle_validate_swarm_views(const void* scene, const OracleParams* p, int64_t n_views, const double* views,
+                                const int64_t* self, int64_t n_swarm, const double* swarm, const double* half,
+                                int64_t npix, const int64_t* pix, const int32_t* id, const float* depth,
+                                uint8_t* valid) {
+    if (!half || !self || !swarm) return -1;
+    for (int64_t k = 0; k < n_views; ++k)
+        if (self[k] < 0 || self[k] >= n_swarm) return -1;
+    Swarm sw{swarm, n_swarm, {half[0], half[1], half[2]}, {0, 0, 0}, self};
+    return validate_impl(static_cast<const OracleScene*>(scene), p, n_views, views, &sw, npix, pix, id, depth, valid);
 }
 
 // Pairwise proximity of a swarm [Sec. III-B: collisions among the drones of

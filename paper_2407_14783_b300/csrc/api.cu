@@ -519,6 +519,7 @@ void swarm_free(sim_ctx* c, SwarmScratch& w) {
     ctx_free(c, w.spheres, (size_t)w.cap_agents * sizeof(float4));
     ctx_free(c, w.off, sizeof(int) * ((size_t)w.cap_scenes + 1));
     ctx_free(c, w.cursor, sizeof(int) * ((size_t)w.cap_scenes + 1));
+    ctx_free(c, w.groups, 2 * sizeof(float4) * swarm_group_slots(w.cap_agents, w.cap_scenes));
     w = SwarmScratch{};
 }
 // Grow w to n agents and `rows` scene rows.  Growing synchronises the device
@@ -528,17 +529,20 @@ int swarm_reserve(sim_ctx* c, SwarmScratch& w, int n, int rows) {
     const int na = std::max(std::max(n, w.cap_agents), 1), ns = std::max(std::max(rows, w.cap_scenes), 1);
     cudaDeviceSynchronize();
     swarm_free(c, w);
-    void *a = nullptr, *b = nullptr, *o = nullptr, *u = nullptr, *sp = nullptr;
+    void *a = nullptr, *b = nullptr, *o = nullptr, *u = nullptr, *sp = nullptr, *gr = nullptr;
+    const size_t gbytes = 2 * sizeof(float4) * swarm_group_slots(na, ns);
     int rc;
     if ((rc = ctx_alloc(c, (size_t)na * 3 * sizeof(float4), &a)) || (rc = ctx_alloc(c, (size_t)na * sizeof(int), &b)) ||
         (rc = ctx_alloc(c, sizeof(int) * ((size_t)ns + 1), &o)) || (rc = ctx_alloc(c, sizeof(int) * ((size_t)ns + 1), &u)) ||
-        (rc = ctx_alloc(c, (size_t)na * sizeof(float4), &sp))) {
+        (rc = ctx_alloc(c, (size_t)na * sizeof(float4), &sp)) || (rc = ctx_alloc(c, gbytes, &gr))) {
         ctx_free(c, a, (size_t)na * 3 * sizeof(float4));
         ctx_free(c, b, (size_t)na * sizeof(int));
         ctx_free(c, o, sizeof(int) * ((size_t)ns + 1));
         ctx_free(c, u, sizeof(int) * ((size_t)ns + 1));
+        ctx_free(c, sp, (size_t)na * sizeof(float4));
         return rc;
     }
+    w.groups = (float4*)gr;
     w.spheres = (float4*)sp;
     w.drones = (float4*)a;
     w.members = (int*)b;
@@ -569,8 +573,10 @@ int do_render(sim_ctx* c, int n, const int32_t* soa, const float* state, float* 
         }
         if (!w || !w->off || n > w->cap_agents || a.n_scenes > w->cap_scenes)
             return fail(SIM_ERR_INVALID_ARG, "multi-agent buffers too small for this launch");
-        const cudaError_t e = launch_swarm_prep(n, soa, state, a.n_scenes, *w, s);
+        cudaError_t e = launch_swarm_prep(n, soa, state, a.n_scenes, *w, s);
+        if (e == cudaSuccess && n > kSwarmGroupMin) e = launch_swarm_groups(n, a.n_scenes, *w, s);
         if (e != cudaSuccess) return cuda_fail(e, "swarm preparation");
+        a.swarm_groups = n > kSwarmGroupMin ? w->groups : nullptr;
         const sim_swarm& sc = c->swarm_cfg;
         a.drones = w->drones;
         a.swarm_off = w->off;

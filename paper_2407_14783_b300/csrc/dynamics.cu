@@ -783,6 +783,9 @@ __device__ __forceinline__ void load_cmd(const float* __restrict__ u_, int n, in
 template <bool GEO>
 __global__ void __launch_bounds__(128) step_kernel(DynConsts c, int n, float* state, const float* __restrict__ cmd,
                                                    float* __restrict__ ckpt) {
+    // a render launched next as a programmatic dependent may start its
+    // prologue now; it waits for this grid to finish before reading the state
+    asm volatile("griddepcontrol.launch_dependents;");
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= n) return;
     float y[17], u[4];

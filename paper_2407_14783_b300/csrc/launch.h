@@ -115,6 +115,7 @@ struct RenderArgs {
     const float4* drones = nullptr;
     const int* swarm_off = nullptr;
     const float4* swarm_spheres = nullptr;  // per member, in member order: (centre, agent index as int bits)
+    const float4* swarm_groups = nullptr;   // member groups of the larger swarms (SwarmScratch::groups) or null
     float swarm_half[3] = {0.0f, 0.0f, 0.0f};
     float swarm_radius = 0.0f;   // |swarm_half|: bounding sphere for the per-tile cull
     uint32_t swarm_rgb = 0;      // packed like the scene colours
@@ -128,10 +129,24 @@ struct SwarmScratch {
     float4* spheres = nullptr; // [cap_agents]: member centres with the agent index in w
     int* off = nullptr;        // [cap_scenes + 1]
     int* cursor = nullptr;     // [cap_scenes]
+    float4* groups = nullptr;  // [swarm_group_slots(cap_agents, cap_scenes)][2]: member groups' centre bounds
     int cap_agents = 0, cap_scenes = 0;
 };
+// Two-level hierarchy over a scene's swarm members (rebuilt every launch):
+// scenes with more than kSwarmGroupMin members have their members ordered
+// along a Morton curve and cut into groups of 32 consecutive members; group g
+// of scene s is entry (off[s] / 32 + s + g) of `groups` (lo, hi of the member
+// centres).  A tile tests the groups' boxes before their members.
+constexpr int kSwarmGroupMin = 256;
+constexpr int kSwarmSortMax = 4096;  // members per scene that are sorted; beyond that, groups in bucket order
+inline size_t swarm_group_slots(int cap_agents, int cap_scenes) {
+    return (size_t)cap_agents / 32 + (size_t)cap_scenes + 2;
+}
 cudaError_t launch_swarm_prep(int n, const int* scene_of_agent, const float* state, int n_scenes, SwarmScratch& s,
                               cudaStream_t st);
+// After launch_swarm_prep: order each larger swarm along a Morton curve and
+// write its groups' boxes (one CTA per scene).
+cudaError_t launch_swarm_groups(int n, int n_scenes, SwarmScratch& s, cudaStream_t st);
 cudaError_t launch_swarm_proximity(int n, const int* scene_of_agent, const float* state, int n_scenes,
                                    const SwarmScratch& s, float radius, float* dist, int* other, int* n_collide,
                                    cudaStream_t st);

@@ -31,7 +31,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kTmin = 1e-6f;
 constexpr int kIterCap = 1 << 18;  // node + leaf visits per work item
-constexpr int kStack = 64;
+constexpr int kStack = 64;  // traversal stack entries of the counted, streamed, multi-agent and 4-wide builds
 constexpr int kWarpsPerCta = 4;
 constexpr int kSplit = 4;  // sub-packets (quarter tiles) of a very heavy tile
 
@@ -239,12 +239,23 @@ __global__ void __launch_bounds__(256) sched_estimate_kernel(RenderArgs A, int T
     // (every thread, before any early exit: the ray cast's own wait relies on
     // this kernel finishing only after that work)
     asm volatile("griddepcontrol.launch_dependents;");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int lane = threadIdx.x & 31;
     const int n = A.n_agents;
     const int W = A.cam.W, H = A.cam.H;
     const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH, tiles = tiles_x * tiles_y;
     const long long total = (long long)n * tiles;
+    {
+        // while the previous kernel (the dynamics step) finishes: pull the last
+        // launch's costs and attitudes into L2 (a hint, no data is read yet)
+        const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        if (t * 32 < total && total <= A.sched_cap) asm volatile("prefetch.global.L2 [%0];" ::"l"(A.cost + t * 32));
+        if (t * 8 < n && n <= A.sched_cap) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(A.pose + t * 8));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(A.pose + (size_t)A.sched_cap + t * 8));
+        }
+        if (t == 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(A.sched));
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (total > A.sched_cap) return;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // agent-major: t = agent * tiles + p
     const bool act = t < total;
@@ -336,15 +347,19 @@ __global__ void __launch_bounds__(256) sched_estimate_kernel(RenderArgs A, int T
     }
 }
 
-template <int TW, int TH, int RPL, bool SMEM_STACK, bool STAGE, bool COUNT, bool WIDE, int EXTRA>
+// STACK: the warp's traversal stack entries.  In registers a stack of 32 takes
+// one register per lane (entry k in lane k), 64 take two; in shared memory it
+// is STACK ints per warp.  A scene deeper than the stack is refused on the host.
+template <int TW, int TH, int RPL, bool SMEM_STACK, bool STAGE, bool COUNT, bool WIDE, int EXTRA, int STACK>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6) raycast_kernel(RenderArgs A) {
+    static_assert(STACK > 0 && STACK <= 64 && (SMEM_STACK || STACK % 32 == 0), "stack depth");
     static_assert(TW * TH == 32 * RPL, "tile must hold 32 * RPL pixels");
     extern __shared__ float4 smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* stage = smem + warp * 12;
-    int* sstack = reinterpret_cast<int*>(smem + kWarpsPerCta * 12) + warp * kStack;
+    int* sstack = reinterpret_cast<int*>(smem + kWarpsPerCta * 12) + warp * STACK;
     uint8_t* rgbstage = reinterpret_cast<uint8_t*>(reinterpret_cast<int*>(smem + kWarpsPerCta * 12) +
-                                                   kWarpsPerCta * kStack) + warp * (32 * RPL * 3);
+                                                   kWarpsPerCta * STACK) + warp * (32 * RPL * 3);
 
     const int W = A.cam.W, H = A.cam.H;
     const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
@@ -582,13 +597,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                 const int m_lo = __ldg(A.swarm_off + sid), m_hi = __ldg(A.swarm_off + sid + 1);
                 const float rad = A.swarm_radius;
                 const float4 none = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(agent));
-                // two groups of 32 members per pass, both loads in flight together
-                for (int k0 = m_lo; k0 < m_hi; k0 += 64) {
+                // members k0 .. k1 - 1 (at most 64): cull their bounding spheres
+                // against the tile's bounds, test each survivor's box
+                auto members = [&](int k0, int k1) {
                     float4 sph[2];
 #pragma unroll
                     for (int g = 0; g < 2; ++g) {
                         const int k = k0 + 32 * g + lane;
-                        sph[g] = k < m_hi ? __ldg(A.swarm_spheres + k) : none;
+                        sph[g] = k < k1 ? __ldg(A.swarm_spheres + k) : none;
                     }
 #pragma unroll
                     for (int g = 0; g < 2; ++g) {
@@ -607,6 +623,30 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                             for (int q = 0; q < RPL; ++q) drone_test(ray[q], c0, c1, c2, A.swarm_half, INT_MIN + jj);
                         }
                     }
+                };
+                if (A.swarm_groups && m_hi - m_lo > kSwarmGroupMin) {
+                    // a larger swarm: cull its groups of 32 first (their centre
+                    // bounds grown by the drones' radius)
+                    const int n_g = (m_hi - m_lo + 31) / 32;
+                    const float4* gb = A.swarm_groups + 2 * ((size_t)m_lo / 32 + sid);
+                    for (int g0 = 0; g0 < n_g; g0 += 32) {
+                        const int g = g0 + lane;
+                        bool keep = false;
+                        if (g < n_g) {
+                            const float4 l = __ldg(gb + 2 * g), h = __ldg(gb + 2 * g + 1);
+                            keep = l.x - rad <= bhi[0] && h.x + rad >= blo[0] && l.y - rad <= bhi[1] &&
+                                   h.y + rad >= blo[1] && l.z - rad <= bhi[2] && h.z + rad >= blo[2];
+                        }
+                        unsigned gm = __ballot_sync(kFull, keep);
+                        while (gm) {
+                            const int gg = g0 + __ffs(gm) - 1;
+                            gm &= gm - 1;
+                            const int k0 = m_lo + 32 * gg;
+                            members(k0, min(k0 + 32, m_hi));
+                        }
+                    }
+                } else {
+                    for (int k0 = m_lo; k0 < m_hi; k0 += 64) members(k0, min(k0 + 64, m_hi));
                 }
             }
             // large triangles: cull against the tile's ray-segment bounds, test the rest
@@ -708,7 +748,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                         for (int q = 0; q < RPL; ++q) c_need_nodes += need[q] ? 1 : 0;
                     }
                     if (cnt > 0) {
-                        if (sp + cnt - 1 > kStack) {
+                        if (sp + cnt - 1 > STACK) {
                             if (lane == 0) set_error(A.err, kDevErrTraversal);
                             break;
                         }
@@ -718,7 +758,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                             if (SMEM_STACK) {
                                 if (lane == 0) sstack[sp] = far;
                             } else if (lane == (sp & 31)) {
-                                if (sp < 32) reg0 = far; else reg1 = far;
+                                if (STACK <= 32 || sp < 32) reg0 = far; else reg1 = far;
                             }
                             if (COUNT) {
                                 const int sl = j == 3 ? slot[3] : j == 2 ? slot[2] : slot[1];
@@ -777,14 +817,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                         const bool near1 = 2 * __popc(__ballot_sync(kFull, pref1)) > __popc(b0 & b1);
                         const int far = near1 ? c0 : c1;
                         next = near1 ? c1 : c0;
-                        if (sp >= kStack) {
+                        if (sp >= STACK) {
                             if (lane == 0) set_error(A.err, kDevErrTraversal);
                             break;
                         }
                         if (SMEM_STACK) {
                             if (lane == 0) sstack[sp] = far;
                         } else if (lane == (sp & 31)) {
-                            if (sp < 32) reg0 = far; else reg1 = far;
+                            if (STACK <= 32 || sp < 32) reg0 = far; else reg1 = far;
                         }
                         if (COUNT) {
 #pragma unroll
@@ -825,7 +865,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                         __syncwarp();
                         next = sstack[sp];
                     } else {
-                        next = __shfl_sync(kFull, sp < 32 ? reg0 : reg1, sp & 31);
+                        next = __shfl_sync(kFull, (STACK <= 32 || sp < 32) ? reg0 : reg1, sp & 31);
                     }
                     if (COUNT) {
 #pragma unroll
@@ -986,21 +1026,36 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
     }
 }
 
-template <int TW, int TH, int RPL, bool SMEM_STACK, bool STAGE, bool COUNT, bool WIDE, int EXTRA>
+template <int TW, int TH, int RPL, bool SMEM_STACK, bool STAGE, bool COUNT, bool WIDE, int EXTRA, int STACK>
 cudaError_t launch_one(const RenderArgs& a, int ctas, cudaStream_t s) {
-    auto k = raycast_kernel<TW, TH, RPL, SMEM_STACK, STAGE, COUNT, WIDE, EXTRA>;
-    const size_t shm = render_smem_bytes(kWarpsPerCta, kStack, RPL);
+    auto k = raycast_kernel<TW, TH, RPL, SMEM_STACK, STAGE, COUNT, WIDE, EXTRA, STACK>;
+    const size_t shm = render_smem_bytes(kWarpsPerCta, STACK, RPL);
     return launch_cfg(reinterpret_cast<const void*>(k), a, kWarpsPerCta, ctas, shm, s);
+}
+
+// The stack depth is a tuning choice of the device render (binary nodes, no
+// counters, no streamed download, no drones); the other builds keep kStack
+// entries, which holds any scene the configured depth admits.  Traversal order
+// does not depend on the stack's size, so images and counts are the same.
+template <int TW, int TH, int RPL, bool SMEM_STACK, bool STAGE, bool COUNT, bool WIDE, int EXTRA>
+cudaError_t launch_stack(const RenderArgs& a, const sim_render_config& c, int ctas, cudaStream_t s) {
+    if constexpr (!COUNT && !WIDE && EXTRA == 0) {
+        if (c.stack_depth == 32) return launch_one<TW, TH, RPL, SMEM_STACK, STAGE, COUNT, WIDE, EXTRA, 32>(a, ctas, s);
+        if constexpr (SMEM_STACK)
+            if (c.stack_depth == 48)
+                return launch_one<TW, TH, RPL, SMEM_STACK, STAGE, COUNT, WIDE, EXTRA, 48>(a, ctas, s);
+    }
+    return launch_one<TW, TH, RPL, SMEM_STACK, STAGE, COUNT, WIDE, EXTRA, kStack>(a, ctas, s);
 }
 
 template <int TW, int TH, int RPL, bool COUNT, bool WIDE, int EXTRA>
 cudaError_t launch_shape_w(const RenderArgs& a, const sim_render_config& c, int ctas, cudaStream_t s) {
     if (c.stack_in_smem) {
-        if (c.stage_in_smem) return launch_one<TW, TH, RPL, true, true, COUNT, WIDE, EXTRA>(a, ctas, s);
-        return launch_one<TW, TH, RPL, true, false, COUNT, WIDE, EXTRA>(a, ctas, s);
+        if (c.stage_in_smem) return launch_stack<TW, TH, RPL, true, true, COUNT, WIDE, EXTRA>(a, c, ctas, s);
+        return launch_stack<TW, TH, RPL, true, false, COUNT, WIDE, EXTRA>(a, c, ctas, s);
     }
-    if (c.stage_in_smem) return launch_one<TW, TH, RPL, false, true, COUNT, WIDE, EXTRA>(a, ctas, s);
-    return launch_one<TW, TH, RPL, false, false, COUNT, WIDE, EXTRA>(a, ctas, s);
+    if (c.stage_in_smem) return launch_stack<TW, TH, RPL, false, true, COUNT, WIDE, EXTRA>(a, c, ctas, s);
+    return launch_stack<TW, TH, RPL, false, false, COUNT, WIDE, EXTRA>(a, c, ctas, s);
 }
 
 // EXTRA selects what is compiled in: 0 neither the drone test of the
@@ -1041,17 +1096,27 @@ size_t render_smem_bytes(int warps_per_cta, int stack_depth, int rpl) {
     return (size_t)warps_per_cta * (12 * sizeof(float4) + stack_depth * sizeof(int) + 32 * rpl * 3);
 }
 
+// Stack depths a configuration may take: binary nodes 32 or 64 entries in
+// registers, 32, 48 or 64 in shared memory; 4-wide nodes 64.
+static bool stack_depth_ok(int width, int in_smem, int depth) {
+    if (width == 4) return depth == kStack;
+    if (in_smem) return depth == 32 || depth == 48 || depth == 64;
+    return depth == 32 || depth == 64;
+}
+
 int render_config_list(sim_render_config* out, int max) {
     static const int shapes[][3] = {{8, 4, 1}, {4, 8, 1}, {16, 2, 1}, {8, 8, 2}, {16, 4, 2}};
     int k = 0;
     for (int width : {2, 4})
         for (const auto& sh : shapes)
             for (int stack = 0; stack <= 1; ++stack)
-                for (int stg = 0; stg <= 1; ++stg) {
-                    if (k < max && out)
-                        out[k] = sim_render_config{sh[0], sh[1], sh[2], stack, kStack, kWarpsPerCta, 0, stg, width};
-                    ++k;
-                }
+                for (int depth : {32, 48, 64})
+                    for (int stg = 0; stg <= 1; ++stg) {
+                        if (!stack_depth_ok(width, stack, depth)) continue;
+                        if (k < max && out)
+                            out[k] = sim_render_config{sh[0], sh[1], sh[2], stack, depth, kWarpsPerCta, 0, stg, width};
+                        ++k;
+                    }
     return k;
 }
 
@@ -1061,9 +1126,9 @@ bool render_config_valid(const sim_render_config& c) {
     for (int i = 0; i < n; ++i) {
         const sim_render_config& a = all[i];
         if (a.tile_w == c.tile_w && a.tile_h == c.tile_h && a.rays_per_lane == c.rays_per_lane &&
-            (c.stack_in_smem == 0 || c.stack_in_smem == 1) && (c.stage_in_smem == 0 || c.stage_in_smem == 1) &&
-            c.warps_per_cta == kWarpsPerCta && c.stack_depth == kStack && c.ctas_per_sm >= 0 && c.ctas_per_sm <= 32 &&
-            (c.node_width == 2 || c.node_width == 4))
+            a.stack_in_smem == c.stack_in_smem && a.stack_depth == c.stack_depth && a.node_width == c.node_width &&
+            (c.stage_in_smem == 0 || c.stage_in_smem == 1) && c.warps_per_cta == kWarpsPerCta &&
+            c.ctas_per_sm >= 0 && c.ctas_per_sm <= 32)
             return true;
     }
     return false;

@@ -91,6 +91,140 @@ __global__ void __launch_bounds__(kPrepThreads) swarm_prep_kernel(int n, const i
     }
 }
 
+// 10 bits of v spread three apart (bit i to bit 3 i).
+__device__ __forceinline__ unsigned spread3(unsigned v) {
+    v &= 0x3FFu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__device__ __forceinline__ float block_reduce(float v, bool take_max, float* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = take_max ? fmaxf(v, w) : fminf(v, w);
+    }
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float r = red[0];
+    for (int k = 1; k < nw; ++k) r = take_max ? fmaxf(r, red[k]) : fminf(r, red[k]);
+    return r;
+}
+
+// One CTA per scene: a scene with more than kSwarmGroupMin members (and at
+// most kSwarmSortMax) has them ordered along the Morton curve of their
+// centres (bitonic sort of (code, position) in shared memory, then an
+// in-place permutation of the member and sphere lists), so that 32
+// consecutive members lie close together; then every group of 32 gets the
+// bounds of its members' centres.  Larger swarms keep the bucket order (their
+// groups are looser, the result is the same).  Only the order of members
+// within a scene changes, which neither the ray cast's closest-hit rule nor
+// the proximity query depends on.
+constexpr int kGroupThreads = 512;
+__global__ void __launch_bounds__(kGroupThreads) swarm_group_kernel(const int* __restrict__ off,
+                                                                    int* __restrict__ members,
+                                                                    float4* __restrict__ spheres,
+                                                                    float4* __restrict__ groups) {
+    __shared__ unsigned long long key[kSwarmSortMax];
+    __shared__ float red[kGroupThreads / 32];
+    const int sid = blockIdx.x, tid = threadIdx.x;
+    const int lo = off[sid], m = off[sid + 1] - lo;
+    if (m <= kSwarmGroupMin) return;
+    if (m <= kSwarmSortMax) {
+        float bl[3] = {INFINITY, INFINITY, INFINITY}, bh[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int k = tid; k < m; k += kGroupThreads) {
+            const float4 c = spheres[lo + k];
+            bl[0] = fminf(bl[0], c.x), bl[1] = fminf(bl[1], c.y), bl[2] = fminf(bl[2], c.z);
+            bh[0] = fmaxf(bh[0], c.x), bh[1] = fmaxf(bh[1], c.y), bh[2] = fmaxf(bh[2], c.z);
+        }
+        float L[3], S[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            L[j] = block_reduce(bl[j], false, red);
+            const float h = block_reduce(bh[j], true, red);
+            S[j] = h > L[j] ? 1023.0f / (h - L[j]) : 0.0f;
+        }
+        int p2 = 1;
+        while (p2 < m) p2 <<= 1;
+        for (int k = tid; k < p2; k += kGroupThreads) {
+            unsigned long long v = ~0ull;  // padding sorts last
+            if (k < m) {
+                const float4 c = spheres[lo + k];
+                const unsigned code = (spread3((unsigned)((c.x - L[0]) * S[0])) << 2) |
+                                      (spread3((unsigned)((c.y - L[1]) * S[1])) << 1) |
+                                      spread3((unsigned)((c.z - L[2]) * S[2]));
+                v = ((unsigned long long)code << 32) | (unsigned)k;
+            }
+            key[k] = v;
+        }
+        __syncthreads();
+        for (int size = 2; size <= p2; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int k = tid; k < p2; k += kGroupThreads) {
+                    const int partner = k ^ stride;
+                    if (partner > k) {
+                        const bool up = (k & size) == 0;
+                        const unsigned long long a = key[k], b = key[partner];
+                        if ((a > b) == up) {
+                            key[k] = b;
+                            key[partner] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        // permute in place: everything is read before anything is written
+        constexpr int kPer = kSwarmSortMax / kGroupThreads;
+        float4 sv[kPer];
+        int mv[kPer];
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+            const int k = tid + r * kGroupThreads;
+            if (k < m) {
+                const int src = (int)(key[k] & 0xFFFFFFFFu);
+                sv[r] = spheres[lo + src];
+                mv[r] = members[lo + src];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+            const int k = tid + r * kGroupThreads;
+            if (k < m) {
+                spheres[lo + k] = sv[r];
+                members[lo + k] = mv[r];
+            }
+        }
+        __syncthreads();
+    }
+    // group boxes, one warp per group of 32 consecutive members
+    const int lane = tid & 31, warp = tid >> 5, n_g = (m + 31) / 32;
+    float4* gb = groups + 2 * ((size_t)lo / 32 + sid);
+    for (int g = warp; g < n_g; g += kGroupThreads / 32) {
+        const int k = g * 32 + lane;
+        float4 c = k < m ? spheres[lo + k] : spheres[lo + g * 32];
+        float l0 = c.x, l1 = c.y, l2 = c.z, h0 = c.x, h1 = c.y, h2 = c.z;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            l0 = fminf(l0, __shfl_xor_sync(0xffffffffu, l0, o));
+            l1 = fminf(l1, __shfl_xor_sync(0xffffffffu, l1, o));
+            l2 = fminf(l2, __shfl_xor_sync(0xffffffffu, l2, o));
+            h0 = fmaxf(h0, __shfl_xor_sync(0xffffffffu, h0, o));
+            h1 = fmaxf(h1, __shfl_xor_sync(0xffffffffu, h1, o));
+            h2 = fmaxf(h2, __shfl_xor_sync(0xffffffffu, h2, o));
+        }
+        if (lane == 0) {
+            gb[2 * g] = make_float4(l0, l1, l2, 0.0f);
+            gb[2 * g + 1] = make_float4(h0, h1, h2, 0.0f);
+        }
+    }
+}
+
 // Per agent (one warp each, the lanes splitting the scene's members): the
 // nearest other agent of its scene (centre distance; lowest index among equal
 // squared distances) and how many lie closer than 2 radius.
@@ -146,6 +280,12 @@ cudaError_t launch_swarm_prep(int n, const int* scene_of_agent, const float* sta
     if (n <= 0) return cudaSuccess;
     swarm_prep_kernel<<<1, kPrepThreads, 0, st>>>(n, scene_of_agent, state, n_scenes, s.off, s.cursor, s.members,
                                                   s.spheres, s.drones);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_swarm_groups(int n, int n_scenes, SwarmScratch& s, cudaStream_t st) {
+    if (n <= kSwarmGroupMin || n_scenes <= 0) return cudaSuccess;
+    swarm_group_kernel<<<n_scenes, kGroupThreads, 0, st>>>(s.off, s.members, s.spheres, s.groups);
     return cudaGetLastError();
 }
 

@@ -49,16 +49,22 @@ def test_render_parity_large_scene_sampled(make_sim, oracle_mod, wl):
 
 
 def test_render_configs_identical(make_sim, wl):
-    """Every supported tile shape / rays-per-lane / stack placement gives the same
-    images (the closest-hit rule with lowest-id ties is order independent)."""
+    """Every supported tile shape / rays-per-lane / stack placement and depth /
+    node width gives the same images (the closest-hit rule with lowest-id ties
+    is order independent); a stack no deeper than the scene's BVH is refused."""
+    from paper_2407_14783_b300.binding import SimError
     from paper_2407_14783_b300.sim import Sim
     p = wl.params()
     sc = wl.cluttered_scene(n_objects=400, size=(20.0, 20.0, 6.0), seed=4)
     sim = make_sim(p)
     sid = sim.add_workload_scene(sc)
+    depth = sim.scene_info(sid)["depth"]
+    assert 0 < depth < 32
     s = wl.spawn_states(sc, 37, 5, 1100.0).astype(np.float32)
+    cfgs = Sim.render_configs()
+    assert {c["stack_depth"] for c in cfgs} == {32, 48, 64}
     base = None
-    for cfg in Sim.render_configs():
+    for cfg in cfgs:
         sim.set_render_config(cfg)
         out = _render(sim, sid, s)
         if base is None:
@@ -66,6 +72,12 @@ def test_render_configs_identical(make_sim, wl):
         else:
             for a, b in zip(out, base):
                 assert np.array_equal(a, b), cfg
+    # a 2M-triangle scene's tree is deeper than 32 levels: 32-entry stacks are refused
+    big = sim.add_workload_scene(wl.sized_scene(2_000_000, 711))
+    if sim.scene_info(big)["depth"] >= 32:
+        sim.set_render_config({**cfgs[0], "stack_depth": 32, "stack_in_smem": 0, "node_width": 2})
+        with pytest.raises(SimError):
+            _render(sim, sid, s)
 
 
 @pytest.mark.parametrize("wh", [(30, 18), (64, 64), (128, 96), (7, 5)])

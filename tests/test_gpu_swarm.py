@@ -229,3 +229,34 @@ def test_single_agent_swarm_equals_parallel_mode(make_sim, wl):
     swarm = _gpu_render(sim, ids, st)
     for a, b in zip(plain, swarm):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("n,views", [(600, 6), (4200, 3)])
+def test_large_swarm_matches_oracle(make_sim, oracle_mod, wl, n, views):
+    """Swarms large enough for the two-level cull (groups of 32 Morton-ordered
+    members; beyond 4,096 members per scene the groups keep the bucket order):
+    sampled cameras against the oracle rendering the same cameras with the
+    whole swarm visible."""
+    p = wl.params()
+    sc = wl.room_scene()
+    sim = make_sim(p)
+    sid = sim.add_workload_scene(sc)
+    sim.set_swarm(HALF, RGB, LABEL)
+    st = wl.spawn_states(sc, n, 60 + n, 1100.0, clearance=0.2).astype(np.float32)
+    ids = torch.full((n,), sid, dtype=torch.int32, device="cuda")
+    d, c, h = _gpu_render(sim, ids, st)
+    pick = np.random.default_rng(n).choice(n, views, replace=False)
+    osc = oracle_mod.Scene.from_workload(sc)
+    st64 = st.astype(np.float64)
+    sw = {"half": HALF, "rgb": RGB, "states": st64, "self": pick}
+    ref = osc.render(p, st64[pick], swarm=sw)
+    assert (ref["id"] <= -2).sum() > 100 * views       # the other drones fill part of every image
+    rid = ref["id"]
+    clear = ~ref["tie"]
+    assert np.array_equal(h[pick][clear], rid[clear])
+    assert np.array_equal(c[pick][clear], ref["rgb"][clear])
+    assert np.all(np.abs(d[pick][clear] - ref["depth"][clear]) <= DEPTH_TOL * ref["depth"][clear])
+    ties = np.flatnonzero(ref["tie"].ravel())
+    if ties.size:
+        ok = osc.validate(p, st64[pick], ties, h[pick].ravel()[ties], d[pick].ravel()[ties], swarm=sw)
+        assert ok.all(), f"{(~ok).sum()} of {ties.size} tie pixels not admissible"

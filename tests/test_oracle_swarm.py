@@ -170,3 +170,28 @@ def test_proximity_equidistant_takes_lowest_index(oracle_mod):
     assert dist[0] == 2.0 and other[0] == 1 and hits[0] == 3      # all three at 2 < 2 * 2.0
     dist, other, hits = oracle_mod.swarm_proximity(pos, 1.0)
     assert hits[0] == 0                                           # 2 < 2 * 1.0 is false
+
+
+def test_swarm_views_equal_the_full_swarm_render(oracle_mod, wl):
+    """Rendering chosen cameras of a swarm gives exactly those cameras' images
+    of the full swarm render (the views form only selects cameras)."""
+    p = wl.params(width=24, height=16)
+    sc = wl.room_scene()
+    osc = oracle_mod.Scene.from_workload(sc)
+    rng = np.random.default_rng(3)
+    st = wl.spawn_states(sc, 9, 12, 1100.0)
+    st[:, 0:3] = st[0, 0:3] + rng.uniform(-1.0, 1.0, (9, 3))
+    st[:, 2] = np.clip(st[:, 2], 0.6, 3.4)
+    sw = {"half": (0.25, 0.18, 0.06), "rgb": (250, 20, 30)}
+    full = osc.render(p, st, swarm=sw)
+    pick = np.array([7, 2, 5])
+    part = osc.render(p, st[pick], swarm={**sw, "states": st, "self": pick})
+    for k in ("depth", "rgb", "id", "tie"):
+        assert np.array_equal(part[k], full[k][pick]), k
+    assert (part["id"] <= -2).any()
+    # the oracle's own answers are admissible at its ambiguous pixels
+    tie = np.flatnonzero(part["tie"].ravel())
+    pix = tie if tie.size else np.arange(5)
+    ok = osc.validate(p, st[pick], pix, part["id"].ravel()[pix], part["depth"].ravel()[pix].astype(np.float32),
+                      swarm={**sw, "states": st, "self": pick})
+    assert ok.all()
