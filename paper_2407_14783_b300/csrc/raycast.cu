@@ -105,6 +105,14 @@ __device__ __forceinline__ bool slab(const Ray& r, float lx, float ly, float lz,
     return tn <= tf;  // a dead ray has best_t < 0, so it passes no box
 }
 
+// 32 bytes in one read-only load (sm_100 and later): half a binary node, whose
+// records are 64-byte aligned.
+__device__ __forceinline__ void ld_nc_v8(const float4* p, float4& a, float4& b) {
+    asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+                 : "l"(p));
+}
+
 // Fetch `count` (<= 4) consecutive triangle records and test every ray.
 template <int RPL, bool STAGE>
 __device__ __forceinline__ void test_leaf(Ray (&ray)[RPL], const float4* __restrict__ src, int count, float4* stage,
@@ -259,7 +267,8 @@ __global__ void __launch_bounds__(256) sched_estimate_kernel(RenderArgs A, int T
     if (total > A.sched_cap) return;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // agent-major: t = agent * tiles + p
     const bool act = t < total;
-    const int agent = act ? (int)(t / tiles) : 0, p = act ? (int)(t - (long long)agent * tiles) : 0;
+    const unsigned ua = act ? (unsigned)t / (unsigned)tiles : 0u;  // total < 2^31
+    const int agent = (int)ua, p = act ? (int)((unsigned)t - ua * (unsigned)tiles) : 0;
     unsigned long long* S = A.sched;
     const unsigned long long ep = S[kSchedEpoch];
     const bool valid = S[kSchedTotal] == (unsigned long long)total && S[kSchedShape] == sched_shape(tiles_x, tiles_y, n);
@@ -519,10 +528,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
         // rows from the image centre outwards: rows near the horizon (long rays
         // through clutter) are the costly ones, floor and ceiling rows the cheap
         // ones.
-        const int rank = (int)(item / A.n_agents);
-        const int agent = (int)(item - (long long)rank * A.n_agents);
-        const int ty = tile_row_of(rank / tiles_x, tiles_y);
-        const int tx0 = (rank % tiles_x) * TW, ty0 = ty * TH;
+        // item < total < 2^31 (the host refuses larger launches): 32-bit divisions
+        const unsigned uitem = (unsigned)item, un = (unsigned)A.n_agents, utx = (unsigned)tiles_x;
+        const unsigned urank = uitem / un;
+        const int rank = (int)urank;
+        const int agent = (int)(uitem - urank * un);
+        const unsigned urow = urank / utx;
+        const int ty = tile_row_of((int)urow, tiles_y);
+        const int tx0 = (int)(urank - urow * utx) * TW, ty0 = ty * TH;
         const int sid = __ldg(A.scene_of_agent + agent);
         const bool scene_ok = sid >= 0 && sid < A.n_scenes && A.table[sid].live;
         if (!scene_ok && lane == 0) set_error(A.err, kDevErrNotFound);
@@ -690,10 +703,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
             }
             int& iters = item_cost;
             while (cur != kEmptyRoot) {
-                if (++iters > kIterCap) {
-                    if (lane == 0) set_error(A.err, kDevErrTraversal);
-                    break;
-                }
+                ++iters;
                 int next = kEmptyRoot;
                 if (WIDE && cur >= 0) {
                     // 4-wide node: SoA child boxes, codes in w[6]
@@ -790,10 +800,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                         n2 = stage[2];
                         n3 = stage[3];
                     } else {
-                        n0 = __ldg(np);
-                        n1 = __ldg(np + 1);
-                        n2 = __ldg(np + 2);
-                        n3 = __ldg(np + 3);
+                        ld_nc_v8(np, n0, n1);
+                        ld_nc_v8(np + 2, n2, n3);
                     }
                     bool h0 = false, h1 = false, pref1 = false;
                     bool ha[RPL], hb[RPL];
@@ -860,6 +868,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                 }
                 if (next == kEmptyRoot) {
                     if (sp == 0) break;
+                    // the cap is checked where the walk pops: between two pops
+                    // it only descends, at most the tree's depth
+                    if (iters > kIterCap) {
+                        if (lane == 0) set_error(A.err, kDevErrTraversal);
+                        break;
+                    }
                     --sp;
                     if (SMEM_STACK) {
                         __syncwarp();
