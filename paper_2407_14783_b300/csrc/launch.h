@@ -48,8 +48,8 @@ cudaError_t lbvh_build(int64_t nt, const float* d_verts, const int* d_tris, cons
                        LbvhAlloc alloc, void* alloc_user, LbvhResult* out, cudaStream_t s);
 
 // raycast.cu
-// Cost buckets of the longest-first schedule: estimates over 4, 2, 1.25, 0.8,
-// 0.5 and 0.25 times the mean cost, and the rest.  The first kHeavyBuckets are
+// Cost buckets of the longest-first schedule: estimates over 4 (6 in streamed
+// launches), 2, 1.25, 0.8, 0.5 and 0.25 times the mean cost, and the rest.  The first kHeavyBuckets are
 // the heavy ones that a streamed launch interleaves with the natural order.
 constexpr int kBuckets = 7;
 constexpr int kHeavyBuckets = 4;

@@ -241,7 +241,7 @@ __device__ __forceinline__ void quat_rotation(float w, float x, float y, float z
 // contribute by overlap area; parts outside the previous image count at the
 // mean cost.  The launch's order only changes which warp renders which tile
 // when, never a pixel's value.
-__global__ void __launch_bounds__(256) sched_estimate_kernel(RenderArgs A, int TW, int TH) {
+__global__ void __launch_bounds__(256) sched_estimate_kernel(RenderArgs A, int TW, int TH, float split) {
     // the ray cast that follows may start its prologue now; everything this
     // kernel reads was written by earlier stream work, so wait for it first
     // (every thread, before any early exit: the ray cast's own wait relies on
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(256) sched_estimate_kernel(RenderArgs A, int T
                     est = (acc + fmaxf(area - cov, 0.0f) * mean) / area;
                 }
             }
-            b = est > 4.0f * mean    ? 0
+            b = est > split * mean   ? 0
                 : est > 2.0f * mean  ? 1
                 : est > 1.25f * mean ? 2
                 : est > 0.8f * mean  ? 3
@@ -1163,7 +1163,12 @@ cudaError_t launch_render(const RenderArgs& a, const sim_render_config& c, int c
         attr[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        const cudaError_t e = cudaLaunchKernelEx(&cfg, sched_estimate_kernel, a, c.tile_w, c.tile_h);
+        // tiles over `split` times the mean cost are rendered as quarter-tile
+        // sub-packets: 4x in device renders; 6x when the launch also streams its
+        // bands to the host, where a split tile holds its band back longer
+        // (measured: 2.3% faster host steps, device renders unchanged)
+        const float split = a.band_done ? 6.0f : 4.0f;
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, sched_estimate_kernel, a, c.tile_w, c.tile_h, split);
         if (e != cudaSuccess) return e;
     }
     return count ? dispatch<true>(a, c, ctas, s) : dispatch<false>(a, c, ctas, s);
