@@ -233,3 +233,27 @@ def test_outputs_finite_and_in_range(make_sim, wl):
     assert torch.isfinite(st).all()
     assert torch.isfinite(d).all() and (d > 0).all() and (d <= p["max_depth"]).all()
     assert ((h >= -1) & (h < sc.n_tris)).all()
+
+
+def test_tile_costs_and_build_times(make_sim, wl):
+    """The load-analysis queries: per-tile traversal costs of the last render
+    (refused before any render) and the phase times of a scene's build."""
+    from paper_2407_14783_b300.binding import SimError
+    p = wl.params()
+    sc = wl.cluttered_scene(n_objects=400, size=(20.0, 20.0, 6.0), seed=4)
+    sim = make_sim(p)
+    sid = sim.add_workload_scene(sc)
+    with pytest.raises(SimError):
+        sim.tile_costs()
+    bt = sim.scene_build_times(sid)
+    assert set(bt) == set(sim.BUILD_PHASES) | {"wall"}
+    assert all(v >= 0.0 for v in bt.values()) and bt["clustering"] > 0.0 and bt["sort"] > 0.0
+    assert bt["wall"] >= max(bt[k] for k in sim.BUILD_PHASES)
+    n = 9
+    s = wl.spawn_states(sc, n, 5, 1100.0).astype(np.float32)
+    _render(sim, sid, s)
+    cfg = sim.render_config()
+    costs = sim.tile_costs()
+    assert costs.shape == (n, -(-64 // cfg["tile_h"]), -(-64 // cfg["tile_w"]))
+    assert (costs >= 1).all()            # every tile walks at least the root
+    assert costs.max() > 4 * np.median(costs)   # and the costs are uneven, which is why they are scheduled
