@@ -229,7 +229,7 @@ def _recorded_profile():
                              (kv.split("=", 1) for kv in line.split(";") if "=" in kv))
                 if parts.get("raycast_cu_sha1", "") == sha:
                     out = {"traffic": int(parts["dram_bytes_per_launch"])}
-                    for k in ("issue_active", "alu_pipe", "l2_throughput", "dram_throughput"):
+                    for k in ("issue_active", "alu_pipe", "l2_throughput", "dram_throughput", "warp_inst_per_launch"):
                         if k in parts:
                             out[k] = float(parts[k])
                     return out
@@ -326,7 +326,7 @@ def controller_extra(sim, p, spawn, n, u_h):
     return out
 
 
-def raycast_roofline(sim, cnt, n, p, render_ms):
+def raycast_roofline(sim, cnt, n, p, render_ms, sm_mhz=None):
     """Roofline of the dominant kernel.  Algorithmic bytes per launch (per agent-frame:
     4096 rays x (N_node * 64 B + N_tri * 48 B + 7 B output) + 28 B of pose), with
     N_node / N_tri the nodes and triangles each ray's own walk needs (counter build),
@@ -361,7 +361,26 @@ def raycast_roofline(sim, cnt, n, p, render_ms):
             # what limits the kernel in the committed ncu capture of this source:
             # instruction issue, not L2 or DRAM bandwidth
             "ncu": {k: prof[k] for k in ("issue_active", "alu_pipe", "l2_throughput", "dram_throughput")
-                    if k in prof} or None}
+                    if k in prof} or None,
+            "issue": issue_roofline(prof, render_ms, sm_mhz)}
+
+
+def issue_roofline(prof, render_ms, sm_mhz):
+    """The bound the ray cast actually meets: instruction issue.  Warp
+    instructions of one launch (the committed ncu capture of this source, same
+    workload) over the launch's CUDA-event time, against the SMs' issue peak of
+    one warp instruction per cycle per scheduler (the device's SMs x 4
+    schedulers x the SM clock sampled during the timed steps)."""
+    import torch
+    inst = prof.get("warp_inst_per_launch")
+    if not inst or not sm_mhz:
+        return None
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    achieved = inst / (render_ms * 1e-3) / 1e9
+    peak = sms * 4 * sm_mhz * 1e-3
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "G warp-instructions/s",
+            "frac": achieved / peak, "warp_inst_per_launch": inst,
+            "peak_kind": "SMs x 4 schedulers x 1 instruction per cycle at the sampled SM clock"}
 
 
 def run_ours(args):
@@ -511,8 +530,8 @@ def run_ours(args):
     cnt = sim.render(ids, state, depth, rgb, counted=True)
     counted_states = state.T.double().cpu().numpy()   # the oracle's BVH walks the same rays (cpu_baseline leg)
     render_ms = statistics.mean(ren_ms)
-    roof = raycast_roofline(sim, cnt, n, p, render_ms)
     clocks = clk.summary()
+    roof = raycast_roofline(sim, cnt, n, p, render_ms, clocks.get("sm_mhz"))
 
     # nearest-obstacle query (the paper's obstacle-distance module) on the same
     # agents: 20 calls captured in a CUDA graph, so the device time is measured
