@@ -16,6 +16,7 @@ agents in its own copy of the scene (weak scaling, no data-path collective).
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -429,6 +430,10 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    # no Python garbage collection inside the timed steps: a collection pause
+    # between an event and the launches after it would show as GPU time
+    gc.collect()
+    gc.disable()
     with ClockSampler(dev.index if ws == 1 else local) as clk:
         for k in range(K):
             t = W + k
@@ -441,6 +446,7 @@ def run_ours(args):
             sim.render(ids, state, depth, rgb)
             e2.record(stream)
         torch.cuda.synchronize()
+    gc.enable()
     if ws > 1:
         dist.barrier()
     sim.check()
@@ -492,6 +498,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
+        gc.collect()
+        gc.disable()
         t0 = time.perf_counter()
         for k in range(K2):
             if k % EPISODE == 0:
@@ -499,6 +507,7 @@ def run_ours(args):
             step(W + k)
             stream.synchronize()        # the host reads the observation every step
         e2e_s = time.perf_counter() - t0
+        gc.enable()
         if ws > 1:
             t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
