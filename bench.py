@@ -327,11 +327,11 @@ def controller_extra(sim, p, spawn, n, u_h):
     return out
 
 
-def raycast_roofline(sim, cnt, n, p, render_ms, sm_mhz=None):
+def raycast_roofline(sim, cnt, n, p, launch_ms, sm_mhz=None):
     """Roofline of the dominant kernel.  Algorithmic bytes per launch (per agent-frame:
     4096 rays x (N_node * 64 B + N_tri * 48 B + 7 B output) + 28 B of pose), with
     N_node / N_tri the nodes and triangles each ray's own walk needs (counter build),
-    over the average launch time, against this GPU's L2 read bandwidth measured by
+    over the ray-cast kernel's average launch time, against this GPU's L2 read bandwidth measured by
     the library's probe (the scene is L2-resident)."""
     rays = cnt["rays"]
     items = max(cnt["items"], 1)
@@ -340,30 +340,30 @@ def raycast_roofline(sim, cnt, n, p, render_ms, sm_mhz=None):
     need_tris = (cnt["need_tri_tests"] + cnt["large_tests"] * rays_per_item) / rays
     per_ray = need_nodes * 64 + need_tris * 48 + 7
     alg_bytes = rays * per_ray + n * 28
-    achieved = alg_bytes / (render_ms * 1e-3) / 1e9
+    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
     # the peak is the best of five probe runs (single runs vary by several per cent)
     l2 = max(sim.probe_read_bandwidth(64 << 20, iters=20) for _ in range(5))
     hbm, hbm_kind = _peaks()
     prof = _recorded_profile()
     traffic = prof.get("traffic")
-    hbm_achieved = traffic / (render_ms * 1e-3) / 1e9 if traffic else None
+    hbm_achieved = traffic / (launch_ms * 1e-3) / 1e9 if traffic else None
     return {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
             "traffic": traffic, "kernel": "raycast_kernel",
             "hbm_achieved": hbm_achieved, "hbm_frac": hbm_achieved / hbm if hbm_achieved else None,
             "peak_kind": "L2 read bandwidth measured in this run (sim_probe_read_bandwidth, 64 MiB resident, "
                          "best of 5)",
             "hbm_peak": hbm, "hbm_peak_kind": hbm_kind, "alg_bytes_per_launch": alg_bytes,
-            "launch_ms": render_ms,
+            "launch_ms": launch_ms,
             "per_ray": {"need_nodes": need_nodes, "need_tris": need_tris, "bytes": per_ray},
             "per_item": {"rays": rays_per_item, "node_fetches": cnt["node_visits"] / items,
                          "tri_fetches": cnt["tri_tests"] / items, "large_tests": cnt["large_tests"] / items},
             "packet_demand_gbs": (cnt["node_visits"] * 64 + (cnt["tri_tests"] + cnt["large_tests"]) * 48)
-                                 * rays_per_item / (render_ms * 1e-3) / 1e9,
+                                 * rays_per_item / (launch_ms * 1e-3) / 1e9,
             # what limits the kernel in the committed ncu capture of this source:
             # instruction issue, not L2 or DRAM bandwidth
             "ncu": {k: prof[k] for k in ("issue_active", "alu_pipe", "l2_throughput", "dram_throughput")
                     if k in prof} or None,
-            "issue": issue_roofline(prof, render_ms, sm_mhz)}
+            "issue": issue_roofline(prof, launch_ms, sm_mhz)}
 
 
 def issue_roofline(prof, render_ms, sm_mhz):
@@ -412,6 +412,8 @@ def run_ours(args):
     # warm-up (also selects the render configuration by autotuning on this workload)
     tune = None
     if args.no_autotune:
+        if args.render_config:
+            sim.set_render_config({**sim.render_config(), **json.loads(args.render_config)})
         best = sim.render_config()
     else:
         best, times = sim.autotune(ids, state, depth, rgb, iters=3)
@@ -470,6 +472,20 @@ def run_ours(args):
     torch.cuda.synchronize()
     dyn_ms = [a.elapsed_time(b) for a, b, c in evb]
     ren_ms = [b.elapsed_time(c) for a, b, c in evb]
+    # The ray-cast kernel alone (the roofline's launch time): the library
+    # records a CUDA event just before and just after the kernel, after its
+    # estimate kernel, in every launch of one more pass of the same loop.
+    state.copy_(spawn)
+    sim.kernel_timing(True)
+    for k in range(len(evb)):
+        t = W + k
+        if t % EPISODE == 0:
+            state.copy_(spawn)
+        flush.zero_()
+        sim.step(state, cmds[t])
+        sim.render(ids, state, depth, rgb)
+    kern_ms = [float(x) for x in sim.kernel_times()]
+    sim.kernel_timing(False)
     total_s = sum(step_ms) / 1e3
     if ws > 1:
         t = torch.tensor([total_s], device=dev, dtype=torch.float64)
@@ -539,8 +555,11 @@ def run_ours(args):
     cnt = sim.render(ids, state, depth, rgb, counted=True)
     counted_states = state.T.double().cpu().numpy()   # the oracle's BVH walks the same rays (cpu_baseline leg)
     render_ms = statistics.mean(ren_ms)
+    kernel_ms = statistics.mean(kern_ms)
     clocks = clk.summary()
-    roof = raycast_roofline(sim, cnt, n, p, render_ms, clocks.get("sm_mhz"))
+    roof = raycast_roofline(sim, cnt, n, p, kernel_ms, clocks.get("sm_mhz"))
+    roof["render_ms"] = render_ms
+    roof["frac_of_render"] = roof["achieved"] * kernel_ms / render_ms / roof["peak"]
 
     # nearest-obstacle query (the paper's obstacle-distance module) on the same
     # agents: 20 calls captured in a CUDA graph, so the device time is measured
@@ -576,9 +595,11 @@ def run_ours(args):
                        "triangles": int(scene.n_tris), "l2": "flushed between timed steps (256 MiB write)",
                        "reset_every_steps": EPISODE, "render_config": best, "autotune_ms": tune,
                        "bvh_depth": sim.scene_info(sid)["depth"]},
-            "e2e": e2e, "gpu_launches": 2 * K,
-            "breakdown_ms": {"dynamics": statistics.mean(dyn_ms), "render": render_ms,
-                             "from": "a separate pass of %d steps with an event between the two" % len(evb)},
+            "e2e": e2e, "gpu_launches": 3 * K,   # per step: dynamics, tile-cost estimate, ray cast
+            "breakdown_ms": {"dynamics": statistics.mean(dyn_ms), "render": render_ms, "raycast_kernel": kernel_ms,
+                             "from": "a separate pass of %d steps with an event between the two; the ray-cast "
+                                     "kernel alone from a third pass with events around it "
+                                     "(sim_kernel_timing)" % len(evb)},
             "roofline": roof,
             "extras": {"nearest_obstacle": {"agents": n, "ms": near_ms, "queries_per_s": n / (near_ms * 1e-3)},
                        "sensors": sensors, "controllers": controllers},
@@ -774,7 +795,7 @@ def batched_leg(p, scenes, steps, warmup, compare_fixed=True, iters_tune=3, grou
            "scene_bytes": int(sum(sim.scene_info(i)["bytes"] for i in sids)),
            "bvh_depth_max": int(max(sim.scene_info(i)["depth"] for i in sids)),
            "autotuned_config": best, "bvh_build_s": build_s, "clocks": results["autotuned"]["clk"],
-           "gpu_launches": steps * T * 2}
+           "gpu_launches": steps * T * 3}   # per step: dynamics, tile-cost estimate, ray cast
     if compare_fixed:
         out["fixed_config"] = fixed
         out["fixed_value"] = results["fixed_8x4"]["value"]
@@ -1006,7 +1027,7 @@ def run_swarm(args):
                        "swarm_over_parallel_time": ms_swarm / ms_plain,
                        "l2": "flushed between timed steps (256 MiB write)"},
             "swarm_sizes": sweep,
-            "gpu_launches": 7 * args.steps}
+            "gpu_launches": 6 * args.steps}   # per step: dynamics, swarm prep, estimate, ray cast, 2 proximity
     print(json.dumps(line), flush=True)
     return 0
 
@@ -1183,6 +1204,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--no-autotune", action="store_true", help="use the default ray-cast configuration")
+    ap.add_argument("--render-config", default=None,
+                    help="with --no-autotune: JSON fields that replace the default ray-cast configuration's, "
+                         "e.g. '{\"stack_depth\": 32}'")
     ap.add_argument("--no-extra-legs", action="store_true",
                     help="skip the bounded batched and serving legs and the 2M-triangle build of the default run")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="seconds of arrivals per load level")

@@ -182,6 +182,24 @@ int sim_render(sim_ctx* ctx, int32_t n_agents, const int32_t* scene_of_agent, co
  * (no sim_render launch recorded). */
 int sim_render_tile_costs(sim_ctx* ctx, uint32_t* costs, int64_t max_items, int64_t* n_items);
 
+/* Device time of the ray-cast kernel alone, per launch (no counterpart in the
+ * paper; a measurement aid).  With timing on, every ray-cast launch of the
+ * context that is not being captured into a graph -- up to
+ * SIM_KERNEL_TIMING_MAX launches after sim_kernel_timing(ctx, 1) -- records one
+ * CUDA event just before the kernel (after its estimate kernel) and one just
+ * after it, on the launch's stream; the event before it also ends the
+ * kernel's overlap with the estimate kernel, so a timed launch is, if
+ * anything, slower.  Enabling (again) or disabling clears the record; the
+ * first enable creates 2 * SIM_KERNEL_TIMING_MAX events.
+ * sim_kernel_times waits for the recorded launches and writes the first
+ * min(max, recorded) times in launch order to ms (host float, milliseconds);
+ * *count receives the number recorded, and the record is cleared.
+ * Errors: INVALID_ARG (null ctx or count, ms NULL with max > 0, negative max),
+ * CUDA (event creation or read-back). */
+#define SIM_KERNEL_TIMING_MAX 1024
+int sim_kernel_timing(sim_ctx* ctx, int32_t enable);
+int sim_kernel_times(sim_ctx* ctx, float* ms, int32_t max, int32_t* count);
+
 /* As sim_render with every agent in one scene. */
 int sim_render_scene(sim_ctx* ctx, int32_t n_agents, int32_t scene_id, const float* state, float* depth,
                      uint8_t* rgb, int32_t* hit_id, void* stream);
@@ -441,8 +459,8 @@ int sim_server_destroy(sim_server* srv);
  *   shared memory, 0: stack spread over the warp's registers); stack_depth, the
  *   traversal stack's entries: 32 or 64 in registers (one or two registers a
  *   lane), 32, 48 or 64 in shared memory, 64 with 4-wide nodes -- a scene whose
- *   BVH is as deep as the stack is refused (INVALID_ARG), and the autotuner
- *   skips such configurations; warps_per_cta must be 4; ctas_per_sm (persistent grid =
+ *   BVH is deeper than a binary stack (as deep as a 4-wide one) is refused
+ *   (INVALID_ARG), and the autotuner skips such configurations; warps_per_cta must be 4; ctas_per_sm (persistent grid =
  *   ctas_per_sm * SM count; 0 = as many as fit); stage_in_smem (1: node and
  *   triangle records are fetched by a few lanes with coalesced float4 loads
  *   into shared memory and read back by all lanes; 0: every lane loads the

@@ -115,6 +115,8 @@ SIGNATURES = {
     "sim_render": [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
     "sim_render_scene": [_vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp],
     "sim_render_tile_costs": [_vp, _vp, _i64, _P(_i64)],
+    "sim_kernel_timing": [_vp, _i32],
+    "sim_kernel_times": [_vp, _vp, _i32, _P(_i32)],
     "sim_render_ex": [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "sim_scene_set_labels": [_vp, _i32, _vp, _i64],
     "sim_set_noise": [_vp, _vp],

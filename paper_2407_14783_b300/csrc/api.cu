@@ -138,6 +138,14 @@ struct sim_ctx {
     vf::SwarmScratch swarm;
     int stage_n = 0;
     size_t stage_bytes = 0;
+    // device time of each ray-cast launch alone (sim_kernel_timing): event
+    // pairs recorded around the kernel, one pair per launch, in launch order
+    struct {
+        std::mutex mu;
+        std::atomic<bool> on{false};
+        std::vector<cudaEvent_t> t0, t1;
+        int used = 0;
+    } ktime;
 };
 
 namespace {
@@ -352,6 +360,17 @@ int upload_table(sim_ctx* c) {
     return SIM_OK;
 }
 
+// Whether a configuration's traversal stack holds every walk of scenes up to
+// `depth` levels (internal levels plus the leaf level).  A binary walk pushes
+// at most one entry per internal node on its current root path, and such a
+// path holds at most `depth` internal nodes (the deepest internal node's
+// children are leaves), so depth <= stack_depth suffices.  A 4-wide node
+// pushes up to three; its rule keeps one entry of slack and the kernel's own
+// overflow check reports the rest.
+bool stack_fits(const sim_render_config& cf, int depth) {
+    return cf.node_width == 2 ? depth <= cf.stack_depth : depth < cf.stack_depth;
+}
+
 int max_scene_depth(const sim_ctx* c) {
     std::lock_guard<std::mutex> lk(const_cast<sim_ctx*>(c)->mu);
     int d = 0;
@@ -452,7 +471,7 @@ int check_render_args(sim_ctx* c, int n, const void* soa, const void* state) {
     if (n > 0 && (!soa || !state)) return fail(SIM_ERR_INVALID_ARG, "null scene_of_agent or state");
     const long long tiles = (long long)((c->cam.W + 7) / 4) * ((c->cam.H + 7) / 2);
     if ((long long)n * tiles >= (1ll << 31)) return fail(SIM_ERR_INVALID_ARG, "too many agents for one launch");
-    if (max_scene_depth(c) >= c->rcfg.stack_depth)
+    if (!stack_fits(c->rcfg, max_scene_depth(c)))
         return fail(SIM_ERR_INVALID_ARG, "a scene BVH is deeper than the traversal stack");
     return SIM_OK;
 }
@@ -598,7 +617,19 @@ int do_render(sim_ctx* c, int n, const int32_t* soa, const float* state, float* 
     if (sched_mem) sched_attach(a, sched_mem, sched_cap);
     int ctas = 0;
     if (cfg.ctas_per_sm > 0) ctas = cfg.ctas_per_sm * c->num_sms;
-    cudaError_t e = launch_render(a, cfg, ctas, count, s);
+    cudaEvent_t k0 = nullptr, k1 = nullptr;
+    if (c->ktime.on) {
+        // not inside a stream capture: there an event would time the capture
+        std::lock_guard<std::mutex> lk(c->ktime.mu);
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (c->ktime.on && c->ktime.used < (int)c->ktime.t0.size() && cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
+            cs == cudaStreamCaptureStatusNone) {
+            k0 = c->ktime.t0[c->ktime.used];
+            k1 = c->ktime.t1[c->ktime.used];
+            ++c->ktime.used;
+        }
+    }
+    cudaError_t e = launch_render(a, cfg, ctas, count, s, k0, k1);
     if (e != cudaSuccess) return cuda_fail(e, "ray-cast launch");
     return SIM_OK;
 }
@@ -724,6 +755,10 @@ int sim_destroy_ctx(sim_ctx* c) {
     ctx_free(c, c->d_rgb, 0);
     ctx_free(c, c->d_band, 0);
     swarm_free(c, c->swarm);
+    for (size_t i = 0; i < c->ktime.t0.size(); ++i) {
+        cudaEventDestroy(c->ktime.t0[i]);
+        cudaEventDestroy(c->ktime.t1[i]);
+    }
     delete c;
     return SIM_OK;
 }
@@ -940,6 +975,43 @@ int sim_render_ex(sim_ctx* c, int32_t n, const int32_t* soa, const float* state,
     const sim_render_config cfg = c->rcfg;
     if ((rc = ctx_sched(c, render_items(c, n, cfg), s))) return rc;
     return do_render(c, n, soa, state, depth, rgb, hit, false, cfg, s, nullptr, c->sched_mem, c->sched_cap, seg);
+}
+
+int sim_kernel_timing(sim_ctx* c, int32_t enable) {
+    if (!c) return fail(SIM_ERR_INVALID_ARG, "null context");
+    std::lock_guard<std::mutex> lk(c->ktime.mu);
+    if (enable && c->ktime.t0.empty()) {
+        DeviceGuard g(c->device);
+        for (int i = 0; i < SIM_KERNEL_TIMING_MAX; ++i) {
+            cudaEvent_t a = nullptr, b = nullptr;
+            cudaError_t e = cudaEventCreate(&a);
+            if (e == cudaSuccess) e = cudaEventCreate(&b);
+            if (e != cudaSuccess) {
+                if (a) cudaEventDestroy(a);
+                return cuda_fail(e, "timing events");
+            }
+            c->ktime.t0.push_back(a);
+            c->ktime.t1.push_back(b);
+        }
+    }
+    c->ktime.on = enable != 0;
+    c->ktime.used = 0;
+    return SIM_OK;
+}
+
+int sim_kernel_times(sim_ctx* c, float* ms, int32_t max, int32_t* count) {
+    if (!c || !count || (max > 0 && !ms) || max < 0) return fail(SIM_ERR_INVALID_ARG, "null or negative argument");
+    std::lock_guard<std::mutex> lk(c->ktime.mu);
+    DeviceGuard g(c->device);
+    const int n = c->ktime.used;
+    *count = n;
+    c->ktime.used = 0;
+    for (int i = 0; i < n && i < max; ++i) {
+        cudaError_t e = cudaEventSynchronize(c->ktime.t1[i]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms + i, c->ktime.t0[i], c->ktime.t1[i]);
+        if (e != cudaSuccess) return cuda_fail(e, "kernel timing read-back");
+    }
+    return SIM_OK;
 }
 
 int sim_render_tile_costs(sim_ctx* c, uint32_t* costs, int64_t max_items, int64_t* n_items) {
@@ -1558,7 +1630,7 @@ int sim_autotune_render(sim_ctx* c, int32_t n, const int32_t* soa, const float* 
     }
     for (int i = 0; i < nc; ++i) {
         sim_render_config cf = cfgs[i];
-        if (need_depth >= cf.stack_depth) continue;
+        if (!stack_fits(cf, need_depth)) continue;
         cudaError_t me = cudaMemsetAsync(smem, 0, sched_bytes_for(scap), s);
         if (me != cudaSuccess) {
             rc = cuda_fail(me, "autotune reset");

@@ -153,7 +153,10 @@ cudaError_t launch_swarm_proximity(int n, const int* scene_of_agent, const float
 size_t render_smem_bytes(int warps_per_cta, int stack_depth, int rpl);
 int render_config_list(sim_render_config* out, int max);
 bool render_config_valid(const sim_render_config& c);
-cudaError_t launch_render(const RenderArgs& a, const sim_render_config& c, int ctas, bool count, cudaStream_t s);
+// t0 / t1: events recorded just before and after the ray-cast kernel (after
+// the estimate kernel), or null
+cudaError_t launch_render(const RenderArgs& a, const sim_render_config& c, int ctas, bool count, cudaStream_t s,
+                          cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr);
 // api.cu: context helpers for entry points defined in other files.
 void set_last_error(const char* msg);
 int ctx_device(const sim_ctx* c);

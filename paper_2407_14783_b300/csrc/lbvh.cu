@@ -345,6 +345,18 @@ __device__ __forceinline__ int child_code(int cc, const int2* __restrict__ range
     return cnt <= kLeafMax ? leaf_code(r.x, cnt) : cc;
 }
 
+// Order word of a binary node: 2 * axis + s, axis the one along which the two
+// child boxes' centres lie farthest apart, s = 1 when child 1's centre is the
+// lower one along it.
+__device__ __forceinline__ int order_word(const float4& l0, const float4& h0, const float4& l1, const float4& h1) {
+    const float dx = (l1.x + h1.x) - (l0.x + h0.x), dy = (l1.y + h1.y) - (l0.y + h0.y);
+    const float dz = (l1.z + h1.z) - (l0.z + h0.z);
+    const float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
+    const int axis = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
+    const float d = axis == 0 ? dx : axis == 1 ? dy : dz;
+    return 2 * axis + (d < 0.0f ? 1 : 0);
+}
+
 __global__ void pack_nodes_kernel(int n, const uint32_t* __restrict__ order, const float4* __restrict__ tlo,
                                   const float4* __restrict__ thi, const int2* __restrict__ child,
                                   const int2* __restrict__ range, const float4* __restrict__ node_lo,
@@ -359,7 +371,8 @@ __global__ void pack_nodes_kernel(int n, const uint32_t* __restrict__ order, con
     nodes[4 * (size_t)i + 1] = make_float4(h0.y, h0.z, l1.x, l1.y);
     nodes[4 * (size_t)i + 2] = make_float4(l1.z, h1.x, h1.y, h1.z);
     nodes[4 * (size_t)i + 3] = make_float4(__int_as_float(child_code(c.x, range)),
-                                           __int_as_float(child_code(c.y, range)), 0.0f, 0.0f);
+                                           __int_as_float(child_code(c.y, range)),
+                                           __int_as_float(order_word(l0, h0, l1, h1)), 0.0f);
 }
 
 // Depth parity of every internal node (root: even).
@@ -694,7 +707,8 @@ __global__ void ploc_pack_kernel(int n_int, int m0, const int2* __restrict__ pch
     nodes[4 * (size_t)t + 0] = make_float4(l0.x, l0.y, l0.z, h0.x);
     nodes[4 * (size_t)t + 1] = make_float4(h0.y, h0.z, l1.x, l1.y);
     nodes[4 * (size_t)t + 2] = make_float4(l1.z, h1.x, h1.y, h1.z);
-    nodes[4 * (size_t)t + 3] = make_float4(__int_as_float(c0), __int_as_float(c1), 0.0f, 0.0f);
+    nodes[4 * (size_t)t + 3] = make_float4(__int_as_float(c0), __int_as_float(c1),
+                                           __int_as_float(order_word(l0, h0, l1, h1)), 0.0f);
 }
 
 // 4-wide nodes from packed binary nodes (the same layout pack_wide_kernel

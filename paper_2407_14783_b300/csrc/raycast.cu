@@ -8,8 +8,9 @@
 // lanes with coalesced float4 loads into the warp's shared-memory slot and read
 // back by every lane (STAGE), or loaded by every lane from the same address (a
 // broadcast through L1).  Each lane slab-tests both child boxes against its own
-// rays and a warp vote (__ballot_sync) decides which children any ray needs,
-// near child first, the other pushed on the warp's stack (shared memory or a
+// rays and a warp vote (__ballot_sync) decides which children any ray needs;
+// the near one along the tile's central ray (by the node's stored split axis)
+// is walked first, the other pushed on the warp's stack (shared memory or a
 // stack spread over the lanes' registers).  Leaves (up to 3 triangles, 9
 // float4, contiguous in leaf order) are fetched the same way and every lane runs
 // Moller-Trumbore on them.  The walk ends when the stack is empty; the votes
@@ -599,6 +600,23 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
             ry.best_id = -1;
         }
 
+        // Front-to-back order of a binary node's children: each node stores the
+        // axis along which its children's centres lie farthest apart and which
+        // child is the lower one there (its order word, 2 * axis + s); the tile's
+        // central ray direction decides, per axis, whether the lower child comes
+        // first.  Bit 2 * axis + s of near_bits is set when child 1 is the near
+        // one.  The order changes which nodes the packet skips, never a result.
+        unsigned near_bits;
+        {
+            const float cB[3] = {1.0f, -(float)(2 * tx0 + TW - W) * 0.5f * A.cam.pix,
+                                 -(float)(2 * ty0 + TH - H) * 0.5f * A.cam.pix};
+            near_bits = 0u;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const float dj = R[j][0] * cB[0] + R[j][1] * cB[1] + R[j][2] * cB[2];
+                near_bits |= (dj < 0.0f ? 1u : 2u) << (2 * j);
+            }
+        }
         int item_cost = 0;
         if (scene_ok) {
             // other drones of the scene (multi-agent mode): cull their bounding
@@ -803,7 +821,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                         ld_nc_v8(np, n0, n1);
                         ld_nc_v8(np + 2, n2, n3);
                     }
-                    bool h0 = false, h1 = false, pref1 = false;
+                    bool h0 = false, h1 = false;
                     bool ha[RPL], hb[RPL];
 #pragma unroll
                     for (int q = 0; q < RPL; ++q) {
@@ -812,7 +830,6 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                         hb[q] = slab(ray[q], n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, t1);
                         h0 |= ha[q];
                         h1 |= hb[q];
-                        pref1 |= ha[q] && hb[q] && t1 < t0;
                     }
                     const unsigned b0 = __ballot_sync(kFull, h0), b1 = __ballot_sync(kFull, h1);
                     const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
@@ -822,7 +839,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                         for (int q = 0; q < RPL; ++q) c_need_nodes += need[q] ? 1 : 0;
                     }
                     if (b0 && b1) {
-                        const bool near1 = 2 * __popc(__ballot_sync(kFull, pref1)) > __popc(b0 & b1);
+                        const bool near1 = (near_bits >> __float_as_int(n3.z)) & 1u;
                         const int far = near1 ? c0 : c1;
                         next = near1 ? c1 : c0;
                         if (sp >= STACK) {
@@ -1148,7 +1165,8 @@ bool render_config_valid(const sim_render_config& c) {
     return false;
 }
 
-cudaError_t launch_render(const RenderArgs& a, const sim_render_config& c, int ctas, bool count, cudaStream_t s) {
+cudaError_t launch_render(const RenderArgs& a, const sim_render_config& c, int ctas, bool count, cudaStream_t s,
+                          cudaEvent_t t0, cudaEvent_t t1) {
     if (a.sched && a.n_agents > 0 && c.tile_w > 0 && c.tile_h > 0) {
         const long long items = (long long)a.n_agents * ((a.cam.W + c.tile_w - 1) / c.tile_w) *
                                 ((a.cam.H + c.tile_h - 1) / c.tile_h);
@@ -1171,7 +1189,15 @@ cudaError_t launch_render(const RenderArgs& a, const sim_render_config& c, int c
         const cudaError_t e = cudaLaunchKernelEx(&cfg, sched_estimate_kernel, a, c.tile_w, c.tile_h, split);
         if (e != cudaSuccess) return e;
     }
-    return count ? dispatch<true>(a, c, ctas, s) : dispatch<false>(a, c, ctas, s);
+    // timed launches: events around the ray-cast kernel alone (the one before
+    // it also ends its programmatic overlap with the estimate kernel)
+    if (t0) {
+        const cudaError_t e = cudaEventRecord(t0, s);
+        if (e != cudaSuccess) return e;
+    }
+    const cudaError_t e = count ? dispatch<true>(a, c, ctas, s) : dispatch<false>(a, c, ctas, s);
+    if (e != cudaSuccess || !t1) return e;
+    return cudaEventRecord(t1, s);
 }
 
 }  // namespace vf

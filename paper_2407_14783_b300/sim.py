@@ -210,6 +210,22 @@ class Sim:
         tx, ty = -(-self.W // cfg["tile_w"]), -(-self.H // cfg["tile_h"])
         return out.reshape(-1, ty, tx)
 
+    KERNEL_TIMING_MAX = 1024
+
+    def kernel_timing(self, enable: bool = True):
+        """Record the device time of each following ray-cast launch alone (CUDA
+        events around the kernel; see sim_kernel_timing); clears the record."""
+        B.check(self.L.sim_kernel_timing(self.h, 1 if enable else 0), "sim_kernel_timing", self.h)
+
+    def kernel_times(self) -> np.ndarray:
+        """Milliseconds of each ray-cast launch recorded since timing was turned
+        on (at most KERNEL_TIMING_MAX), in launch order; clears the record."""
+        out = np.zeros(self.KERNEL_TIMING_MAX, np.float32)
+        k = ctypes.c_int32()
+        B.check(self.L.sim_kernel_times(self.h, out.ctypes.data_as(ctypes.c_void_p), len(out), ctypes.byref(k)),
+                "sim_kernel_times", self.h)
+        return out[:min(k.value, len(out))].copy()
+
     def nearest_obstacle(self, scene_of_agent, state, max_dist: float = 10.0, stream=None):
         """Closest mesh point of every agent: (dist [n], point [3, n], tri [n])."""
         n = state.shape[1]

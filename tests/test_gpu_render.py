@@ -51,7 +51,8 @@ def test_render_parity_large_scene_sampled(make_sim, oracle_mod, wl):
 def test_render_configs_identical(make_sim, wl):
     """Every supported tile shape / rays-per-lane / stack placement and depth /
     node width gives the same images (the closest-hit rule with lowest-id ties
-    is order independent); a stack no deeper than the scene's BVH is refused."""
+    is order independent); a binary stack shallower than the scene's BVH is
+    refused."""
     from paper_2407_14783_b300.binding import SimError
     from paper_2407_14783_b300.sim import Sim
     p = wl.params()
@@ -74,10 +75,41 @@ def test_render_configs_identical(make_sim, wl):
                 assert np.array_equal(a, b), cfg
     # a 2M-triangle scene's tree is deeper than 32 levels: 32-entry stacks are refused
     big = sim.add_workload_scene(wl.sized_scene(2_000_000, 711))
-    if sim.scene_info(big)["depth"] >= 32:
+    if sim.scene_info(big)["depth"] > 32:
         sim.set_render_config({**cfgs[0], "stack_depth": 32, "stack_in_smem": 0, "node_width": 2})
         with pytest.raises(SimError):
             _render(sim, sid, s)
+
+
+def test_stack_as_deep_as_tree(make_sim, oracle_mod, wl):
+    """A binary walk holds at most one stack entry per internal node of its root
+    path, so a stack of exactly the tree's depth suffices: the 208,812-triangle
+    scene (a PLOC tree 32 levels deep) renders with 32-entry stacks, in
+    registers and in shared memory, exactly as with 64-entry ones, without a
+    traversal error, and matches the oracle."""
+    from paper_2407_14783_b300.sim import Sim
+    p = wl.params()
+    sc = wl.cluttered_scene(seed=2)
+    sim = make_sim(p)
+    sid = sim.add_workload_scene(sc)
+    depth = sim.scene_info(sid)["depth"]
+    assert 24 <= depth <= 32
+    s = wl.spawn_states(sc, 128, 17, 1100.0).astype(np.float32)
+    cfgs = [c for c in Sim.render_configs() if c["node_width"] == 2 and c["tile_w"] == 8 and c["tile_h"] == 4
+            and c["stage_in_smem"] == 0]
+    ref = None
+    for cfg in sorted(cfgs, key=lambda c: -c["stack_depth"]):
+        sim.set_render_config(cfg)
+        out = _render(sim, sid, s)
+        if ref is None:
+            ref = out
+            pick = np.random.default_rng(5).choice(128, 6, replace=False)
+            compare_images(oracle_mod.Scene.from_workload(sc), p, s[pick].astype(np.float64), out[0][pick],
+                           out[1][pick], out[2][pick])
+        else:
+            for a, b in zip(out, ref):
+                assert np.array_equal(a, b), cfg
+    assert {c["stack_depth"] for c in cfgs} >= {32, 64}
 
 
 @pytest.mark.parametrize("wh", [(30, 18), (64, 64), (128, 96), (7, 5)])
@@ -257,3 +289,27 @@ def test_tile_costs_and_build_times(make_sim, wl):
     assert costs.shape == (n, -(-64 // cfg["tile_h"]), -(-64 // cfg["tile_w"]))
     assert (costs >= 1).all()            # every tile walks at least the root
     assert costs.max() > 4 * np.median(costs)   # and the costs are uneven, which is why they are scheduled
+
+
+def test_kernel_timing(make_sim, wl):
+    """sim_kernel_timing: every ray-cast launch while timing is on records its
+    kernel time (positive, below the whole render's), the images are those of
+    an untimed launch, and reading or disabling clears the record."""
+    p = wl.params()
+    sc = wl.room_scene()
+    sim = make_sim(p)
+    sid = sim.add_workload_scene(sc)
+    s = wl.spawn_states(sc, 64, 8, 1100.0).astype(np.float32)
+    base = _render(sim, sid, s)
+    sim.kernel_timing(True)
+    outs = [_render(sim, sid, s) for _ in range(3)]
+    ms = sim.kernel_times()
+    assert len(ms) == 3 and np.all(ms > 0) and np.all(ms < 1000)
+    for out in outs:
+        for a, b in zip(out, base):
+            assert np.array_equal(a, b)
+    assert len(sim.kernel_times()) == 0
+    _render(sim, sid, s)
+    sim.kernel_timing(False)
+    _render(sim, sid, s)
+    assert len(sim.kernel_times()) == 0

@@ -26,7 +26,7 @@ def _render(sim, ids, s32):
 @pytest.mark.parametrize("n_tris", [1_000_000, 2_000_000])
 def test_render_parity_million_triangle_scene(make_sim, oracle_mod, wl, n_tris):
     """One scene of 1M / 2M triangles (the top of the batched and serving size
-    ranges).  The BVH stays shallower than the traversal stack; 96 agents render
+    ranges).  The BVH fits the traversal stack (no deeper than it); 96 agents render
     in one launch and 4 sampled agents' full images match the oracle."""
     p = wl.params()
     sc = wl.sized_scene(n_tris, 700 + n_tris // 1_000_000)
@@ -34,7 +34,7 @@ def test_render_parity_million_triangle_scene(make_sim, oracle_mod, wl, n_tris):
     sid = sim.add_workload_scene(sc)
     info = sim.scene_info(sid)
     assert info["n_tris"] == sc.n_tris
-    assert 0 < info["depth"] < sim.render_config()["stack_depth"]
+    assert 0 < info["depth"] <= sim.render_config()["stack_depth"]
     n = 96
     s = wl.spawn_states(sc, n, 31, 1100.0).astype(np.float32)
     ids = torch.full((n,), sid, dtype=torch.int32, device="cuda")
@@ -59,7 +59,7 @@ def test_multi_scene_launch_beyond_l2_prefetch(make_sim, oracle_mod, wl):
     traversed = sum(i["n_nodes"] * 64 + i["n_tris"] * 48 for i in infos)
     assert traversed > L2_PREFETCH_LIMIT
     stack = sim.render_config()["stack_depth"]
-    assert all(0 < i["depth"] < stack for i in infos)
+    assert all(0 < i["depth"] <= stack for i in infos)
     counts = wl.zipf_partition(320, len(scenes), 1.1, 41)
     states = [wl.spawn_states(s, int(k), 730 + i, 1100.0).astype(np.float32)
               for i, (s, k) in enumerate(zip(scenes, counts))]
