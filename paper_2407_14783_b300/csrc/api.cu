@@ -469,6 +469,9 @@ int check_render_args(sim_ctx* c, int n, const void* soa, const void* state) {
     if (!c) return fail(SIM_ERR_INVALID_ARG, "null context");
     if (n < 0) return fail(SIM_ERR_INVALID_ARG, "negative agent count");
     if (n > 0 && (!soa || !state)) return fail(SIM_ERR_INVALID_ARG, "null scene_of_agent or state");
+    // items counted with 4 x 2-pixel tiles: a launch of any supported shape
+    // (tiles of 32 pixels or more) then holds fewer than 2^29 items, which the
+    // ray cast's 32-bit work-claim arithmetic relies on
     const long long tiles = (long long)((c->cam.W + 7) / 4) * ((c->cam.H + 7) / 2);
     if ((long long)n * tiles >= (1ll << 31)) return fail(SIM_ERR_INVALID_ARG, "too many agents for one launch");
     if (!stack_fits(c->rcfg, max_scene_depth(c)))

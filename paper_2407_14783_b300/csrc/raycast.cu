@@ -422,8 +422,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
     // Splitting pays only when the launch is short enough for its longest tile
     // to matter: at most 12 tiles per resident warp.
     const bool allow_split = total <= 12ll * gridDim.x * kWarpsPerCta;
-    __shared__ long long s_end[kBuckets];  // cumulative ends of the buckets in the counter's range
-    __shared__ long long s_entries;        // bucket entries (a split tile counts once)
+    // Claim arithmetic is 32-bit: the host admits fewer than 2^31 items counted
+    // with 4 x 2-pixel tiles, so a launch has total < 2^29 items (its tiles hold
+    // 32 pixels or more); bucket ends are clamped below 2^31, and the counter
+    // (at most the bucket ends + total + one overshoot per warp) stays below 2^32.
+    __shared__ unsigned s_end[kBuckets];  // cumulative ends of the buckets in the counter's range
+    __shared__ unsigned s_entries;        // bucket entries (a split tile counts once)
+    const unsigned utotal = (unsigned)total;
     unsigned long long mark = 0;
     unsigned ep = 0;
     if (sched) {
@@ -435,9 +440,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
                 const long long len = (long long)min(A.sched[kSchedLen + b], (unsigned long long)total);
                 end += (b == 0 && allow_split) ? len * kSplit : len;
                 entries += len;
-                s_end[b] = end;
+                s_end[b] = (unsigned)min(end, 0x7FFFFFFFll);
             }
-            s_entries = entries;
+            s_entries = (unsigned)min(entries, 0x7FFFFFFFll);
         }
     } else if (threadIdx.x == 0) {
         for (int b = 0; b < kBuckets; ++b) s_end[b] = 0;
@@ -447,66 +452,74 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
     const bool hinted = s_end[kBuckets - 1] > 0;
     // the buckets held as many entries as the launch has items: the sweep only
     // checks done marks, 32 items per claim
-    const bool sweep = !weave && s_entries >= total;
+    const bool sweep = !weave && s_entries >= utotal;
     unsigned pend = 0u;  // sweep: items of the warp's chunk that are still to render
-    long long pend_base = 0;
+    unsigned pend_base = 0;
     for (;;) {
-        long long item = 0;
+        int item = 0;  // -1: nothing to render this round; utotal: no work left
         int sub = -1;
-        long long chunk = -1;
+        int chunk = -1;
         if (pend) {
-            item = pend_base + (__ffs(pend) - 1);
+            item = (int)(pend_base + (unsigned)(__ffs(pend) - 1));
             pend &= pend - 1;
         } else {
             if (lane == 0) {
-                const long long k = (long long)atomicAdd(A.counter, 1u);
-                // position in the bucket lists, or -1 for a natural-order item at nat
-                long long kb = -1, nat = 0;
+                const unsigned k = atomicAdd(A.counter, 1u);
+                // position kb in the bucket lists, or a natural-order item at nat
+                bool in_buckets = false;
+                unsigned kb = 0, nat = 0;
                 if (!weave) {
-                    if (k < s_end[kBuckets - 1]) kb = k;
+                    in_buckets = k < s_end[kBuckets - 1];
+                    if (in_buckets) kb = k;
                     else nat = k - s_end[kBuckets - 1];
                 } else if (k < s_end[0]) {
+                    in_buckets = true;
                     kb = k;
                 } else {
                     // a streamed launch interleaves the heavy buckets 1.. with the
                     // natural order, which also covers the cheap buckets' tiles
-                    const long long r = k - s_end[0], pair = s_end[kHeavyBuckets - 1] - s_end[0];
-                    if (r < 2 * pair) {
-                        if (r & 1) nat = r >> 1;
-                        else kb = s_end[0] + (r >> 1);
+                    const unsigned r = k - s_end[0], pair = s_end[kHeavyBuckets - 1] - s_end[0];
+                    if ((r >> 1) < pair) {
+                        in_buckets = (r & 1) == 0;
+                        if (in_buckets) kb = s_end[0] + (r >> 1);
+                        else nat = r >> 1;
                     } else {
                         nat = r - pair;
                     }
                 }
-                if (kb < 0 && sweep) {
-                    chunk = nat;
-                } else if (kb >= 0) {
+                if (!in_buckets && sweep) {
+                    chunk = (int)min(nat, 0x7FFFFFFFu);
+                } else if (in_buckets) {
                     int b = 0;
                     while (kb >= s_end[b]) ++b;
-                    const long long j = kb - (b == 0 ? 0ll : s_end[b - 1]);
+                    const unsigned j = kb - (b == 0 ? 0u : s_end[b - 1]);
                     const unsigned* list = A.heavy + (size_t)b * A.sched_cap;
+                    unsigned it;
                     if (b == 0 && allow_split) {
-                        item = list[j / kSplit];
+                        it = list[j / kSplit];
                         sub = (int)(j % kSplit);
                     } else {
-                        item = list[j];
+                        it = list[j];
                     }
                     // an entry from a concurrent launch of another size may not fit this one
-                    if (item >= total) item = -1;
-                    else if (b == 0 || !weave) __stcg(A.done + item, mark);
-                    else if (atomicExch(A.done + item, mark) == mark) item = -1;  // taken in natural order
+                    item = it < utotal ? (int)it : -1;
+                    if (item >= 0) {
+                        if (b == 0 || !weave) __stcg(A.done + it, mark);
+                        else if (atomicExch(A.done + it, mark) == mark) item = -1;  // taken in natural order
+                    }
                 } else {
                     // with hints the natural phase holds only tiles the last launch
                     // found cheap, and taking the edge rows first measured faster
                     // (0.8% with moving poses at 4x8 tiles); without hints the
                     // centre rows, where most costly tiles lie, go first
-                    item = (hinted && !weave && nat < total) ? total - 1 - nat : nat;
-                    if (item >= total) {
-                        item = total;  // no work left
-                    } else if (weave) {
-                        if (atomicExch(A.done + item, mark) == mark) item = -1;  // taken from a bucket
-                    } else if (sched && __ldcg(A.done + item) == mark) {
-                        item = -1;  // done from a bucket
+                    const unsigned v = (hinted && !weave && nat < utotal) ? utotal - 1 - nat : nat;
+                    item = (int)min(v, utotal);  // utotal: no work left
+                    if (v < utotal) {
+                        if (weave) {
+                            if (atomicExch(A.done + v, mark) == mark) item = -1;  // taken from a bucket
+                        } else if (sched && __ldcg(A.done + v) == mark) {
+                            item = -1;  // done from a bucket
+                        }
                     }
                 }
             }
@@ -514,15 +527,15 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
             sub = __shfl_sync(kFull, sub, 0);
             chunk = __shfl_sync(kFull, chunk, 0);
             if (chunk >= 0) {
-                if (chunk * 32 >= total) break;
-                const long long it = chunk * 32 + lane;
-                pend = __ballot_sync(kFull, it < total && __ldcg(A.done + it) != mark);
-                pend_base = chunk * 32;
+                if ((unsigned)chunk >= (utotal + 31u) / 32u) break;
+                const unsigned it = (unsigned)chunk * 32u + (unsigned)lane;
+                pend = __ballot_sync(kFull, it < utotal && __ldcg(A.done + it) != mark);
+                pend_base = (unsigned)chunk * 32u;
                 continue;
             }
         }
         if (item < 0) continue;
-        if (item >= total) break;
+        if ((unsigned)item >= utotal) break;
         // after a device-detected fault every warp stops taking work
         if (__shfl_sync(kFull, lane == 0 ? *(volatile int*)A.err : 0, 0) == kDevErrTraversal) break;
         // Item ids run tile position by tile position across all agents, tile
@@ -532,7 +545,6 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? 8 : 6
         // item < total < 2^31 (the host refuses larger launches): 32-bit divisions
         const unsigned uitem = (unsigned)item, un = (unsigned)A.n_agents, utx = (unsigned)tiles_x;
         const unsigned urank = uitem / un;
-        const int rank = (int)urank;
         const int agent = (int)(uitem - urank * un);
         const unsigned urow = urank / utx;
         const int ty = tile_row_of((int)urow, tiles_y);
@@ -1065,9 +1077,10 @@ cudaError_t launch_one(const RenderArgs& a, int ctas, cudaStream_t s) {
 }
 
 // The stack depth is a tuning choice of the device render (binary nodes, no
-// counters, no streamed download, no drones); the other builds keep kStack
-// entries, which holds any scene the configured depth admits.  Traversal order
-// does not depend on the stack's size, so images and counts are the same.
+// counters, no drones; with the streamed download only the 32-entry register
+// stack besides the default); the other builds keep kStack entries, which
+// holds any scene the configured depth admits.  Traversal order does not
+// depend on the stack's size, so images and counts are the same.
 template <int TW, int TH, int RPL, bool SMEM_STACK, bool STAGE, bool COUNT, bool WIDE, int EXTRA>
 cudaError_t launch_stack(const RenderArgs& a, const sim_render_config& c, int ctas, cudaStream_t s) {
     if constexpr (!COUNT && !WIDE && EXTRA == 0) {
@@ -1076,6 +1089,8 @@ cudaError_t launch_stack(const RenderArgs& a, const sim_render_config& c, int ct
             if (c.stack_depth == 48)
                 return launch_one<TW, TH, RPL, SMEM_STACK, STAGE, COUNT, WIDE, EXTRA, 48>(a, ctas, s);
     }
+    if constexpr (!COUNT && !WIDE && EXTRA == 1 && !SMEM_STACK)
+        if (c.stack_depth == 32) return launch_one<TW, TH, RPL, SMEM_STACK, STAGE, COUNT, WIDE, EXTRA, 32>(a, ctas, s);
     return launch_one<TW, TH, RPL, SMEM_STACK, STAGE, COUNT, WIDE, EXTRA, kStack>(a, ctas, s);
 }
 
