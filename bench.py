@@ -230,8 +230,9 @@ def _recorded_profile():
                              (kv.split("=", 1) for kv in line.split(";") if "=" in kv))
                 if parts.get("raycast_cu_sha1", "") == sha:
                     out = {"traffic": int(parts["dram_bytes_per_launch"])}
-                    for k in ("issue_active", "alu_pipe", "l2_throughput", "dram_throughput", "warp_inst_per_launch"):
-                        if k in parts:
+                    for k in parts:
+                        if k in ("issue_active", "alu_pipe", "l2_throughput", "dram_throughput") or \
+                                k.startswith("warp_inst_per_launch"):
                             out[k] = float(parts[k])
                     return out
     except Exception:
@@ -327,7 +328,7 @@ def controller_extra(sim, p, spawn, n, u_h):
     return out
 
 
-def raycast_roofline(sim, cnt, n, p, launch_ms, sm_mhz=None):
+def raycast_roofline(sim, cnt, n, p, launch_ms, sm_mhz=None, cfg=None):
     """Roofline of the dominant kernel.  Algorithmic bytes per launch (per agent-frame:
     4096 rays x (N_node * 64 B + N_tri * 48 B + 7 B output) + 28 B of pose), with
     N_node / N_tri the nodes and triangles each ray's own walk needs (counter build),
@@ -363,24 +364,28 @@ def raycast_roofline(sim, cnt, n, p, launch_ms, sm_mhz=None):
             # instruction issue, not L2 or DRAM bandwidth
             "ncu": {k: prof[k] for k in ("issue_active", "alu_pipe", "l2_throughput", "dram_throughput")
                     if k in prof} or None,
-            "issue": issue_roofline(prof, launch_ms, sm_mhz)}
+            "issue": issue_roofline(prof, launch_ms, sm_mhz, cfg)}
 
 
-def issue_roofline(prof, render_ms, sm_mhz):
+def issue_roofline(prof, launch_ms, sm_mhz, cfg=None):
     """The bound the ray cast actually meets: instruction issue.  Warp
     instructions of one launch (the committed ncu capture of this source, same
-    workload) over the launch's CUDA-event time, against the SMs' issue peak of
-    one warp instruction per cycle per scheduler (the device's SMs x 4
-    schedulers x the SM clock sampled during the timed steps)."""
+    workload, the timed configuration's tile shape where the capture has it)
+    over the launch's CUDA-event time, against the SMs' issue peak of one warp
+    instruction per cycle per scheduler (the device's SMs x 4 schedulers x the
+    SM clock sampled during the timed steps)."""
     import torch
-    inst = prof.get("warp_inst_per_launch")
+    shape = "%dx%d" % (cfg["tile_w"], cfg["tile_h"]) if cfg else None
+    inst = prof.get("warp_inst_per_launch_" + shape) if shape else None
+    source = shape if inst else "8x4"
+    inst = inst or prof.get("warp_inst_per_launch")
     if not inst or not sm_mhz:
         return None
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    achieved = inst / (render_ms * 1e-3) / 1e9
+    achieved = inst / (launch_ms * 1e-3) / 1e9
     peak = sms * 4 * sm_mhz * 1e-3
     return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "G warp-instructions/s",
-            "frac": achieved / peak, "warp_inst_per_launch": inst,
+            "frac": achieved / peak, "warp_inst_per_launch": inst, "captured_tiles": source,
             "peak_kind": "SMs x 4 schedulers x 1 instruction per cycle at the sampled SM clock"}
 
 
@@ -557,7 +562,7 @@ def run_ours(args):
     render_ms = statistics.mean(ren_ms)
     kernel_ms = statistics.mean(kern_ms)
     clocks = clk.summary()
-    roof = raycast_roofline(sim, cnt, n, p, kernel_ms, clocks.get("sm_mhz"))
+    roof = raycast_roofline(sim, cnt, n, p, kernel_ms, clocks.get("sm_mhz"), best)
     roof["render_ms"] = render_ms
     roof["frac_of_render"] = roof["achieved"] * kernel_ms / render_ms / roof["peak"]
 
