@@ -540,11 +540,49 @@ __global__ void ploc_gather_kernel(int n, const uint32_t* __restrict__ off, cons
     clusters[k] = k;
 }
 
+// Round state of the clustering in device memory, so that rounds run back to
+// back without the host: [0] clusters m, [1] pool nodes created so far, [2] set
+// when a round made no progress (the host then keeps the radix tree), [3] / [4]
+// m and created at the start of the round being applied.
+constexpr int kPlocState = 5;
+constexpr int kPlocTile = 1024;  // clusters per block of the mark and apply kernels (one a thread)
+
+__global__ void ploc_state_init_kernel(int* st, int m0) {
+    st[0] = m0;
+    st[1] = 0;
+    st[2] = 0;
+    st[3] = m0;
+    st[4] = 0;
+}
+
 // Nearest neighbour of every cluster within kPlocRadius positions: smallest
 // union surface area, lowest position among equals.
-__global__ void __launch_bounds__(kPlocBlock) ploc_nn_kernel(int m, const int* __restrict__ clusters,
+__device__ __forceinline__ int ploc_nearest(int k, int m, const float4* slo, const float4* shi, int at) {
+    const float4 ml = slo[at], mh = shi[at];
+    float best = INFINITY;
+    int bj = -1;
+    for (int d = -kPlocRadius; d <= kPlocRadius; ++d) {
+        const int j = k + d;
+        if (d == 0 || j < 0 || j >= m) continue;
+        const float4 ol = slo[at + d], oh = shi[at + d];
+        const float4 ul = make_float4(fminf(ml.x, ol.x), fminf(ml.y, ol.y), fminf(ml.z, ol.z), 0.0f);
+        const float4 uh = make_float4(fmaxf(mh.x, oh.x), fmaxf(mh.y, oh.y), fmaxf(mh.z, oh.z), 0.0f);
+        const float a = half_area(ul, uh);
+        if (a < best) {
+            best = a;
+            bj = j;
+        }
+    }
+    return bj;
+}
+
+__global__ void __launch_bounds__(kPlocBlock) ploc_nn_kernel(const int* __restrict__ st,
+                                                             const int* __restrict__ clusters,
                                                              const float4* __restrict__ plo,
                                                              const float4* __restrict__ phi, int* __restrict__ nn) {
+    if (st[2]) return;
+    const int m = st[0];
+    if (blockIdx.x * kPlocBlock >= m) return;
     __shared__ float4 slo[kPlocBlock + 2 * kPlocRadius], shi[kPlocBlock + 2 * kPlocRadius];
     const int base = blockIdx.x * kPlocBlock - kPlocRadius;
     for (int t = threadIdx.x; t < kPlocBlock + 2 * kPlocRadius; t += kPlocBlock) {
@@ -558,62 +596,191 @@ __global__ void __launch_bounds__(kPlocBlock) ploc_nn_kernel(int m, const int* _
     __syncthreads();
     const int k = blockIdx.x * kPlocBlock + threadIdx.x;
     if (k >= m) return;
-    const float4 ml = slo[threadIdx.x + kPlocRadius], mh = shi[threadIdx.x + kPlocRadius];
-    float best = INFINITY;
-    int bj = -1;
-    for (int d = -kPlocRadius; d <= kPlocRadius; ++d) {
-        const int j = k + d;
-        if (d == 0 || j < 0 || j >= m) continue;
-        const float4 ol = slo[threadIdx.x + kPlocRadius + d], oh = shi[threadIdx.x + kPlocRadius + d];
-        const float4 ul = make_float4(fminf(ml.x, ol.x), fminf(ml.y, ol.y), fminf(ml.z, ol.z), 0.0f);
-        const float4 uh = make_float4(fmaxf(mh.x, oh.x), fmaxf(mh.y, oh.y), fmaxf(mh.z, oh.z), 0.0f);
-        const float a = half_area(ul, uh);
-        if (a < best) {
-            best = a;
-            bj = j;
-        }
-    }
-    nn[k] = bj;
+    nn[k] = ploc_nearest(k, m, slo, shi, threadIdx.x + kPlocRadius);
 }
 
-// keep[k]: cluster k survives the round; make[k]: it merges with its (later)
-// mutual nearest neighbour into a new node.  Entry m of both is 0, so an
-// exclusive scan of m + 1 entries ends with the totals.
-__global__ void ploc_mark_kernel(int m, const int* __restrict__ nn, uint32_t* __restrict__ keep,
-                                 uint32_t* __restrict__ make) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k > m) return;
-    if (k == m) {
-        keep[m] = 0u;
-        make[m] = 0u;
-        return;
-    }
-    const int j = nn[k];
-    const bool mutual = j >= 0 && nn[j] == k;
-    keep[k] = (mutual && k > j) ? 0u : 1u;
-    make[k] = (mutual && k < j) ? 1u : 0u;
-}
-
-__global__ void ploc_apply_kernel(int m, int m0, int node_base, const int* __restrict__ clusters,
-                                  const int* __restrict__ nn, const uint32_t* __restrict__ keep_off,
-                                  const uint32_t* __restrict__ make_off, float4* __restrict__ plo,
-                                  float4* __restrict__ phi, int2* __restrict__ pchild, int* __restrict__ out) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+// Cluster k survives the round unless it merges into its earlier mutual
+// nearest neighbour's new node; it makes a new node when its mutual nearest
+// neighbour comes later.
+__device__ __forceinline__ void ploc_fate(int k, int m, const int* __restrict__ nn, bool& keep, bool& make, int& j) {
+    keep = make = false;
+    j = -1;
     if (k >= m) return;
-    const int j = nn[k];
+    j = nn[k];
     const bool mutual = j >= 0 && nn[j] == k;
-    if (mutual && k > j) return;  // merged into cluster j's new node
+    keep = !(mutual && k > j);
+    make = mutual && k < j;
+}
+
+// Exclusive offsets of this thread's keep / make flags within its block of
+// kPlocTile threads: lane ballots, then a scan of the 32 warps' counts.  Every
+// thread of the block calls it.
+__device__ __forceinline__ void ploc_block_offsets(bool keep, bool make, unsigned& koff, unsigned& moff) {
+    __shared__ unsigned wk[32], wm[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned bk = __ballot_sync(0xffffffffu, keep), bm = __ballot_sync(0xffffffffu, make);
+    if (lane == 0) {
+        wk[warp] = __popc(bk);
+        wm[warp] = __popc(bm);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned ck = wk[lane], cm = wm[lane];
+        unsigned vk = ck, vm = cm;
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned tk = __shfl_up_sync(0xffffffffu, vk, off), tm = __shfl_up_sync(0xffffffffu, vm, off);
+            if (lane >= off) {
+                vk += tk;
+                vm += tm;
+            }
+        }
+        wk[lane] = vk - ck;
+        wm[lane] = vm - cm;
+    }
+    __syncthreads();
+    koff = wk[warp] + __popc(bk & lt);
+    moff = wm[warp] + __popc(bm & lt);
+}
+
+// Merge of cluster k (pool id clusters[k]) with its later mutual neighbour j
+// into pool node nid, or k alone; either way the survivor goes to out[koff].
+__device__ __forceinline__ void ploc_apply_one(int k, int j, bool make, unsigned koff, int nid, int m0,
+                                               const int* __restrict__ clusters, float4* __restrict__ plo,
+                                               float4* __restrict__ phi, int2* __restrict__ pchild,
+                                               int* __restrict__ out) {
     int id = clusters[k];
-    if (mutual) {
+    if (make) {
         const int b = clusters[j];
-        const int nid = node_base + (int)make_off[k];
         const float4 al = plo[id], ah = phi[id], bl = plo[b], bh = phi[b];
         plo[nid] = make_float4(fminf(al.x, bl.x), fminf(al.y, bl.y), fminf(al.z, bl.z), 0.0f);
         phi[nid] = make_float4(fmaxf(ah.x, bh.x), fmaxf(ah.y, bh.y), fmaxf(ah.z, bh.z), 0.0f);
         pchild[nid - m0] = make_int2(id, b);
         id = nid;
     }
-    out[keep_off[k]] = id;
+    out[koff] = id;
+}
+
+// Per block of kPlocTile clusters: how many survive the round and how many
+// make a new node.
+__global__ void __launch_bounds__(kPlocTile) ploc_mark_kernel(const int* __restrict__ st, const int* __restrict__ nn,
+                                                              uint2* __restrict__ block_sums) {
+    if (st[2]) return;
+    const int m = st[0];
+    bool keep, make;
+    int j;
+    ploc_fate(blockIdx.x * kPlocTile + threadIdx.x, m, nn, keep, make, j);
+    const unsigned kt = (unsigned)__syncthreads_count(keep), mt = (unsigned)__syncthreads_count(make);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = make_uint2(kt, mt);
+}
+
+// Exclusive scan of the blocks' counts (in place, one block of 1024 threads)
+// and the round's advance: the survivors become the next round's clusters.
+// A round with more than one cluster and no merge sets the failure flag.
+__global__ void __launch_bounds__(1024) ploc_advance_kernel(int* __restrict__ st, int m0, uint2* __restrict__ sums,
+                                                            int nblocks) {
+    if (st[2]) return;
+    __shared__ unsigned pk[1024], pm[1024];
+    const int per = (nblocks + 1023) / 1024;
+    const int b = threadIdx.x * per, e = min(b + per, nblocks);
+    unsigned sk = 0, sm = 0;
+    for (int i = b; i < e; ++i) {
+        sk += sums[i].x;
+        sm += sums[i].y;
+    }
+    pk[threadIdx.x] = sk;
+    pm[threadIdx.x] = sm;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const unsigned vk = threadIdx.x >= off ? pk[threadIdx.x - off] : 0u;
+        const unsigned vm = threadIdx.x >= off ? pm[threadIdx.x - off] : 0u;
+        __syncthreads();
+        pk[threadIdx.x] += vk;
+        pm[threadIdx.x] += vm;
+        __syncthreads();
+    }
+    unsigned rk = pk[threadIdx.x] - sk, rm = pm[threadIdx.x] - sm;
+    for (int i = b; i < e; ++i) {
+        const uint2 v = sums[i];
+        sums[i] = make_uint2(rk, rm);
+        rk += v.x;
+        rm += v.y;
+    }
+    if (threadIdx.x == 1023) {
+        const int m = st[0], created = st[1];
+        const int kept = (int)pk[1023], made = (int)pm[1023];
+        st[3] = m;
+        st[4] = created;
+        if (m > 1 && (kept >= m || created + made > m0 - 1)) {
+            st[2] = 1;
+        } else {
+            st[0] = kept;
+            st[1] = created + made;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kPlocTile) ploc_apply_kernel(const int* __restrict__ st, int m0,
+                                                               const int* __restrict__ clusters,
+                                                               const int* __restrict__ nn,
+                                                               const uint2* __restrict__ block_off,
+                                                               float4* __restrict__ plo, float4* __restrict__ phi,
+                                                               int2* __restrict__ pchild, int* __restrict__ out) {
+    if (st[2]) return;
+    const int m = st[3], created = st[4];
+    if (blockIdx.x * kPlocTile >= m) return;
+    const int k = blockIdx.x * kPlocTile + threadIdx.x;
+    bool keep, make;
+    int j;
+    ploc_fate(k, m, nn, keep, make, j);
+    unsigned koff, moff;
+    ploc_block_offsets(keep, make, koff, moff);
+    if (!keep) return;
+    const uint2 base = block_off[blockIdx.x];
+    ploc_apply_one(k, j, make, base.x + koff, m0 + created + (int)(base.y + moff), m0, clusters, plo, phi, pchild,
+                   out);
+}
+
+// A whole round in one block while at most kPlocTile clusters are left:
+// neighbours (boxes staged in shared memory), fates, offsets, merges and the
+// advance, with the same results as the multi-block kernels.
+__global__ void __launch_bounds__(kPlocTile) ploc_round_small_kernel(int* __restrict__ st, int m0,
+                                                                     const int* __restrict__ clusters,
+                                                                     float4* __restrict__ plo,
+                                                                     float4* __restrict__ phi,
+                                                                     int2* __restrict__ pchild,
+                                                                     int* __restrict__ out) {
+    if (st[2]) return;
+    __shared__ float4 slo[kPlocTile], shi[kPlocTile];
+    __shared__ int snn[kPlocTile];
+    const int m = st[0], created = st[1];
+    const int k = threadIdx.x;
+    if (k < m) {
+        const int id = clusters[k];
+        slo[k] = plo[id];
+        shi[k] = phi[id];
+    }
+    __syncthreads();
+    // the window never leaves [0, m): ploc_nearest skips positions outside it
+    if (k < m) snn[k] = ploc_nearest(k, m, slo, shi, k);
+    __syncthreads();
+    bool keep, make;
+    int j;
+    ploc_fate(k, m, snn, keep, make, j);
+    unsigned koff, moff;
+    ploc_block_offsets(keep, make, koff, moff);
+    const int kept = __syncthreads_count(keep), made = __syncthreads_count(make);
+    if (keep) ploc_apply_one(k, j, make, koff, m0 + created + (int)moff, m0, clusters, plo, phi, pchild, out);
+    if (threadIdx.x == 0) {
+        st[3] = m;
+        st[4] = created;
+        if (m > 1 && (kept >= m || created + made > m0 - 1)) {
+            st[2] = 1;
+        } else {
+            st[0] = kept;
+            st[1] = created + made;
+        }
+    }
 }
 
 // Parent of every internal pool node (internal t = pool id m0 + t) and of
@@ -848,27 +1015,40 @@ cudaError_t ploc_build(int n_bvh, const uint32_t* order, const float4* tlo, cons
     int2* pchild = reinterpret_cast<int2*>(phi + 2 * (size_t)m0);
     ploc_gather_kernel<<<nb(n_bvh, 256), 256, 0, s>>>(n_bvh, w.flag, w.code_at, w.src_at, order, tlo, thi, node_lo,
                                                       node_hi, w.leaf_code_of, plo, phi, w.c0);
+    // Rounds run back to back on the device (round state in misc[16..20]);
+    // the host reads the state back only every few rounds, to size the grids
+    // to the clusters left and to stop.  Rounds after the last merge copy the
+    // single cluster over, so the result is the same however many run.
+    int* st = misc + 16;
+    uint2* sums = reinterpret_cast<uint2*>(w.keep);  // per-block counts, then offsets
+    ploc_state_init_kernel<<<1, 1, 0, s>>>(st, m0);
     int* cur = w.c0;
     int* nxt = w.c1;
-    int m = m0, created = 0;
-    for (int round = 0; m > 1; ++round) {
-        if (round > 4096) return cudaSuccess;
-        ploc_nn_kernel<<<nb(m, kPlocBlock), kPlocBlock, 0, s>>>(m, cur, plo, phi, w.nn);
-        ploc_mark_kernel<<<nb(m + 1, 256), 256, 0, s>>>(m, w.nn, w.keep, w.make);
-        scan_kernel<<<1, 1024, 0, s>>>(w.keep, m + 1);
-        scan_kernel<<<1, 1024, 0, s>>>(w.make, m + 1);
-        ploc_apply_kernel<<<nb(m, 256), 256, 0, s>>>(m, m0, m0 + created, cur, w.nn, w.keep, w.make, plo, phi, pchild,
-                                                     nxt);
+    int known_m = m0, rounds = 0, state[3] = {m0, 0, 0};
+    while (known_m > 1) {
+        if (rounds > 4096) return cudaSuccess;
+        // rounds per read-back: fewer while the rounds are large
+        const int batch = known_m > 65536 ? 2 : known_m > 8192 ? 4 : 8;
+        for (int r = 0; r < batch; ++r) {
+            if (known_m <= kPlocTile) {
+                ploc_round_small_kernel<<<1, kPlocTile, 0, s>>>(st, m0, cur, plo, phi, pchild, nxt);
+            } else {
+                const int g = (int)nb(known_m, kPlocTile);
+                ploc_nn_kernel<<<nb(known_m, kPlocBlock), kPlocBlock, 0, s>>>(st, cur, plo, phi, w.nn);
+                ploc_mark_kernel<<<g, kPlocTile, 0, s>>>(st, w.nn, sums);
+                ploc_advance_kernel<<<1, 1024, 0, s>>>(st, m0, sums, g);
+                ploc_apply_kernel<<<g, kPlocTile, 0, s>>>(st, m0, cur, w.nn, sums, plo, phi, pchild, nxt);
+            }
+            std::swap(cur, nxt);
+            ++rounds;
+        }
         VF_TRY(cudaGetLastError());
-        uint32_t kept, made;
-        VF_TRY(cudaMemcpyAsync(&kept, w.keep + m, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-        VF_TRY(cudaMemcpyAsync(&made, w.make + m, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        VF_TRY(cudaMemcpyAsync(state, st, sizeof(state), cudaMemcpyDeviceToHost, s));
         VF_TRY(cudaStreamSynchronize(s));
-        if ((int)kept >= m || created + (int)made > m0 - 1) return cudaSuccess;
-        created += (int)made;
-        m = (int)kept;
-        std::swap(cur, nxt);
+        if (state[2]) return cudaSuccess;  // a round without progress: keep the radix tree
+        known_m = state[0];
     }
+    const int created = state[1];
     const int n_int = m0 - 1;
     if (created != n_int) return cudaSuccess;
     timer.mark(5, s);
@@ -935,8 +1115,8 @@ cudaError_t lbvh_build(int64_t nt, const float* d_verts, const int* d_tris, cons
     float4* node_lo = (float4*)take(sizeof(float4) * n);
     float4* node_hi = (float4*)take(sizeof(float4) * n);
     int* flags = (int*)take(sizeof(int) * n);
-    int* misc = (int*)take(sizeof(int) * 16);  // [0..5] bounds, [6..11] centroid bounds, 12 n_large, 13 depth,
-                                               // 14 clustered-tree depth
+    int* misc = (int*)take(sizeof(int) * 32);  // [0..5] bounds, [6..11] centroid bounds, 12 n_large, 13 depth,
+                                               // 14 clustered-tree depth, [16..20] clustering round state
     PlocScratch pw;
     pw.src_at = (int*)take(sizeof(int) * n);
     pw.flag = (uint32_t*)take(sizeof(uint32_t) * ((size_t)n + 1));
@@ -1042,7 +1222,7 @@ size_t lbvh_scratch_bytes(int64_t nt) {
     const size_t nblocks = (n + kSortTile - 1) / kSortTile;
     auto r = [](size_t b) { return (b + 255) & ~(size_t)255; };
     return 2 * r(16 * n) + 5 * r(4 * n) + r(4 * 256 * nblocks) + 2 * r(8 * n) + 2 * r(4 * n) + 2 * r(16 * n) +
-           r(4 * n) + r(64) +
+           r(4 * n) + r(128) +
            // clustering: src_at, flag, leaf_code_of, c0, nn
            r(4 * n) + r(4 * (n + 1)) + 3 * r(4 * n);
 }
