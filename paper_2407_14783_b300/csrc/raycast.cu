@@ -541,8 +541,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? (EXTR
         }
         if (item < 0) continue;
         if ((unsigned)item >= utotal) break;
-        // after a device-detected fault every warp stops taking work
-        if (__shfl_sync(kFull, lane == 0 ? *(volatile int*)A.err : 0, 0) == kDevErrTraversal) break;
+        // after a device-detected fault every warp stops taking work: the error
+        // word is read here and tested when the item is done, so the read's
+        // latency overlaps the item
+        int err_seen = 0;
+        if (lane == 0) asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(err_seen) : "l"(A.err));
         // Item ids run tile position by tile position across all agents, tile
         // rows from the image centre outwards: rows near the horizon (long rays
         // through clutter) are the costly ones, floor and ceiling rows the cheap
@@ -1017,6 +1020,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? (EXTR
                 if (A.host_rgb && A.rgb) copy_out(A.rgb + 3 * first, A.host_rgb + 3 * first, 3 * px, lane);
             }
         }
+        if (__shfl_sync(kFull, err_seen, 0) == kDevErrTraversal) break;
         if (COUNT) ++c_items;
         if (sched && lane == 0) {
             // record this tile's cost for the next launch's schedule; a split
