@@ -360,11 +360,11 @@ __global__ void __launch_bounds__(256) sched_estimate_kernel(RenderArgs A, int T
 // STACK: the warp's traversal stack entries.  In registers a stack of 32 takes
 // one register per lane (entry k in lane k), 64 take two; in shared memory it
 // is STACK ints per warp.  A scene deeper than the stack is refused on the host.
-template <int TW, int TH, int RPL, bool SMEM_STACK, bool STAGE, bool COUNT, bool WIDE, int EXTRA, int STACK>
 // Resident CTAs per SM the register budget is set for: 8 (64 registers) for
 // one ray per lane, 9 (56) for the streamed build, whose host stores and
 // completion fences gain from the extra warps (environment step +1.5%, while
 // the device-only render loses 2% at 9), 6 for two rays per lane or 4-wide nodes.
+template <int TW, int TH, int RPL, bool SMEM_STACK, bool STAGE, bool COUNT, bool WIDE, int EXTRA, int STACK>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? (EXTRA == 1 ? 9 : 8) : 6)
     raycast_kernel(RenderArgs A) {
     static_assert(STACK > 0 && STACK <= 64 && (SMEM_STACK || STACK % 32 == 0), "stack depth");
