@@ -986,8 +986,9 @@ struct PlocScratch {
     int* c0;            // [n]
     int* c1;            // [n]   (the spare sort values buffer)
     int* nn;            // [n]   (later the depth of every internal node)
-    uint32_t* keep;     // [n]   (the sorted keys, dead after the hierarchy)
-    uint32_t* make;     // [n]   (the spare sort keys buffer)
+    uint32_t* keep;     // [n]   rounds' per-block counts, then subtree sizes (the sorted keys, dead after the
+                        //       hierarchy)
+    uint32_t* make;     // [n]   arrival flags of the size pass (the spare sort keys buffer)
 };
 
 // Rebuild the tree above the radix tree's leaves by PLOC and pack it into
