@@ -313,3 +313,20 @@ def test_kernel_timing(make_sim, wl):
     sim.kernel_timing(False)
     _render(sim, sid, s)
     assert len(sim.kernel_times()) == 0
+    # launches captured into a graph (a step loop) record no events, and the
+    # loop's replays record none either; eager launches after it still do
+    from paper_2407_14783_b300.sim import to_soa
+    n = s.shape[0]
+    ids = torch.full((n,), sid, dtype=torch.int32, device="cuda")
+    st = to_soa(s)
+    cmds = torch.zeros((3, 4, n), dtype=torch.float32, device="cuda")
+    d = torch.zeros((2, n, p["height"], p["width"]), dtype=torch.float32, device="cuda")
+    sim.kernel_timing(True)
+    loop = sim.make_loop(ids, st, cmds, d)
+    loop.launch()
+    torch.cuda.synchronize()
+    assert len(sim.kernel_times()) == 0
+    _render(sim, sid, s)
+    assert len(sim.kernel_times()) == 1
+    loop.close()
+    sim.kernel_timing(False)
