@@ -158,15 +158,22 @@ __device__ __forceinline__ float unit_open(unsigned long long x) {
     return ((float)(x >> 40) + 0.5f) * (1.0f / 16777216.0f);
 }
 __device__ __forceinline__ float unit_half_open(unsigned long long x) { return (float)(x >> 40) * (1.0f / 16777216.0f); }
-// Box-Muller with the hardware logarithm and cosine (__logf, __cosf): their
-// errors move a Gaussian draw by about 1e-5 absolute at most (near u1 = 1),
-// far inside the depth tolerance and the rounding band of colour and labels;
-// with every noise model on the render is 12% faster than with logf/cospif.
-// cos(2 pi u2) is taken as -cos(2 pi (u2 - 1/2)), whose argument lies in
-// [-pi, pi), the range the hardware cosine is accurate on.
+// Box-Muller with the hardware logarithm and cosine (__logf, __cosf).  The
+// hardware logarithm's error is absolute (a few 1e-7), so near u1 = 1, where
+// -log u1 itself is small, -log u1 comes from the Mercator series of
+// -log(1 - v) in v = 1 - u1 (exact in FP32 for these uniforms) instead: five
+// terms for v < 1/16 keep it within 2e-7 relative, and the logarithm's
+// relative error elsewhere stays below 6e-6, so a draw moves by under 2e-5
+// absolute, far inside the depth tolerance and the rounding band of colour
+// and labels.  cos(2 pi u2) is taken as -cos(2 pi (u2 - 1/2)), whose argument
+// lies in [-pi, pi), the range the hardware cosine is accurate on.  With every
+// noise model on the render is 9% faster than with logf / cospif.
 __device__ __forceinline__ float gauss_at(unsigned long long seed, unsigned long long i) {
     const float u1 = unit_open(splitmix64_at(seed, i)), u2 = unit_half_open(splitmix64_at(seed, i + 1));
-    return -sqrtf(-2.0f * __logf(u1)) * __cosf(6.2831853f * (u2 - 0.5f));
+    const float v = 1.0f - u1;
+    const float series = v * (1.0f + v * (0.5f + v * (1.0f / 3.0f + v * (0.25f + v * 0.2f))));
+    const float nl = v < 0.0625f ? series : -__logf(u1);
+    return -sqrtf(2.0f * nl) * __cosf(6.2831853f * (u2 - 0.5f));
 }
 // shot (Gaussian form: mean k x, variance k x, scaled back), additive, speckle,
 // salt & pepper, then clamp to [0, hi]
