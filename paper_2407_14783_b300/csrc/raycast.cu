@@ -661,8 +661,52 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? (EXTR
                 const int m_lo = __ldg(A.swarm_off + sid), m_hi = __ldg(A.swarm_off + sid + 1);
                 const float rad = A.swarm_radius;
                 const float4 none = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(agent));
+                // Side planes of the tile's frustum: through the camera origin and
+                // the rays of two neighbouring corner pixels, normals (unit length)
+                // pointing inward.  Every ray of the tile (or of a quarter of it) lies
+                // in the cone of its corner pixels' rays.  A one-pixel-wide or -high
+                // tile gives a zero normal, which culls nothing.  Used for the larger
+                // swarms (the grouped ones): 4,096 drones 6.08 -> 3.59 ms per step,
+                // 1,024 0.94 -> 0.84 ms; at 256 the planes cost more than they save.
+                const bool grouped = A.swarm_groups && m_hi - m_lo > kSwarmGroupMin;
+                float fn[4][3] = {};
+                if (grouped) {
+                    const int cx[4] = {tx0, min(tx0 + TW, W) - 1, min(tx0 + TW, W) - 1, tx0};
+                    const int cy[4] = {ty0, ty0, min(ty0 + TH, H) - 1, min(ty0 + TH, H) - 1};
+                    float cd[4][3];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float b1 = -(float)(2 * cx[k] + 1 - W) * 0.5f * A.cam.pix;
+                        const float b2 = -(float)(2 * cy[k] + 1 - H) * 0.5f * A.cam.pix;
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) cd[k][j] = R[j][0] + R[j][1] * b1 + R[j][2] * b2;
+                    }
+                    const float mid[3] = {cd[0][0] + cd[2][0], cd[0][1] + cd[2][1], cd[0][2] + cd[2][2]};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float* u = cd[k];
+                        const float* w = cd[(k + 1) & 3];
+                        float nx = u[1] * w[2] - u[2] * w[1], ny = u[2] * w[0] - u[0] * w[2], nz = u[0] * w[1] - u[1] * w[0];
+                        const float l2 = nx * nx + ny * ny + nz * nz;
+                        const float sgn = nx * mid[0] + ny * mid[1] + nz * mid[2] < 0.0f ? -1.0f : 1.0f;
+                        const float inv = l2 > 0.0f ? sgn * rsqrtf(l2) : 0.0f;
+                        fn[k][0] = nx * inv;
+                        fn[k][1] = ny * inv;
+                        fn[k][2] = nz * inv;
+                    }
+                }
+                // a sphere that lies wholly outside one side plane misses every
+                // ray of the tile; the slack covers the planes' rounding
+                auto in_frustum = [&](float x, float y, float z, float r) {
+                    const float dx = x - o[0], dy = y - o[1], dz = z - o[2];
+                    const float slack = 1.01f * r + 1e-3f * (1.0f + fabsf(dx) + fabsf(dy) + fabsf(dz));
+                    bool in = true;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) in = in && fn[k][0] * dx + fn[k][1] * dy + fn[k][2] * dz >= -slack;
+                    return in;
+                };
                 // members k0 .. k1 - 1 (at most 64): cull their bounding spheres
-                // against the tile's bounds, test each survivor's box
+                // against the tile's bounds and frustum, test each survivor's box
                 auto members = [&](int k0, int k1) {
                     float4 sph[2];
 #pragma unroll
@@ -675,7 +719,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? (EXTR
                         const int j = __float_as_int(sph[g].w);
                         const bool keep = j != agent && sph[g].x - rad <= bhi[0] && sph[g].x + rad >= blo[0] &&
                                           sph[g].y - rad <= bhi[1] && sph[g].y + rad >= blo[1] &&
-                                          sph[g].z - rad <= bhi[2] && sph[g].z + rad >= blo[2];
+                                          sph[g].z - rad <= bhi[2] && sph[g].z + rad >= blo[2] &&
+                                          (!grouped || in_frustum(sph[g].x, sph[g].y, sph[g].z, rad));
                         unsigned mask = __ballot_sync(kFull, keep);
                         while (mask) {
                             const int src = __ffs(mask) - 1;
@@ -688,7 +733,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? (EXTR
                         }
                     }
                 };
-                if (A.swarm_groups && m_hi - m_lo > kSwarmGroupMin) {
+                if (grouped) {
                     // a larger swarm: cull its groups of 32 first (their centre
                     // bounds grown by the drones' radius)
                     const int n_g = (m_hi - m_lo + 31) / 32;
@@ -700,6 +745,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? (EXTR
                             const float4 l = __ldg(gb + 2 * g), h = __ldg(gb + 2 * g + 1);
                             keep = l.x - rad <= bhi[0] && h.x + rad >= blo[0] && l.y - rad <= bhi[1] &&
                                    h.y + rad >= blo[1] && l.z - rad <= bhi[2] && h.z + rad >= blo[2];
+                            // the group's sphere: its centre box's half diagonal plus the radius
+                            const float ex = 0.5f * (h.x - l.x), ey = 0.5f * (h.y - l.y), ez = 0.5f * (h.z - l.z);
+                            keep = keep && in_frustum(l.x + ex, l.y + ey, l.z + ez, sqrtf(ex * ex + ey * ey + ez * ez) + rad);
                         }
                         unsigned gm = __ballot_sync(kFull, keep);
                         while (gm) {
