@@ -664,8 +664,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? (EXTR
                 // Side planes of the tile's frustum: through the camera origin and
                 // the rays of two neighbouring corner pixels, normals (unit length)
                 // pointing inward.  Every ray of the tile (or of a quarter of it) lies
-                // in the cone of its corner pixels' rays.  A one-pixel-wide or -high
-                // tile gives a zero normal, which culls nothing.  Used for the larger
+                // in the cone of its corner pixels' rays.  An edge between two
+                // corners that are the same pixel (a one-pixel-wide or -high tile)
+                // gets a zero normal, which culls nothing: the cross product of a
+                // ray with itself is not zero once the compiler fuses its products,
+                // so the test is on the pixel indices.  Used for the larger
                 // swarms (the grouped ones): 4,096 drones 6.08 -> 3.59 ms per step,
                 // 1,024 0.94 -> 0.84 ms; at 256 the planes cost more than they save.
                 const bool grouped = A.swarm_groups && m_hi - m_lo > kSwarmGroupMin;
@@ -689,7 +692,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (RPL == 1 && !WIDE) ? (EXTR
                         float nx = u[1] * w[2] - u[2] * w[1], ny = u[2] * w[0] - u[0] * w[2], nz = u[0] * w[1] - u[1] * w[0];
                         const float l2 = nx * nx + ny * ny + nz * nz;
                         const float sgn = nx * mid[0] + ny * mid[1] + nz * mid[2] < 0.0f ? -1.0f : 1.0f;
-                        const float inv = l2 > 0.0f ? sgn * rsqrtf(l2) : 0.0f;
+                        const bool same = cx[k] == cx[(k + 1) & 3] && cy[k] == cy[(k + 1) & 3];
+                        const float inv = !same && l2 > 0.0f ? sgn * rsqrtf(l2) : 0.0f;
                         fn[k][0] = nx * inv;
                         fn[k][1] = ny * inv;
                         fn[k][2] = nz * inv;

@@ -260,3 +260,34 @@ def test_large_swarm_matches_oracle(make_sim, oracle_mod, wl, n, views):
     if ties.size:
         ok = osc.validate(p, st64[pick], ties, h[pick].ravel()[ties], d[pick].ravel()[ties], swarm=sw)
         assert ok.all(), f"{(~ok).sum()} of {ties.size} tie pixels not admissible"
+
+
+@pytest.mark.parametrize("wh", [(7, 5), (1, 9), (9, 1), (30, 18)])
+def test_large_swarm_ragged_tiles_match_oracle(make_sim, oracle_mod, wl, wh):
+    """The larger swarms' frustum cull at image sizes with partial tiles and
+    one-pixel-wide or -high images (tile corners clipped to the image; a
+    degenerate side plane culls nothing): 600 drones, sampled cameras against
+    the oracle."""
+    p = wl.params(width=wh[0], height=wh[1])
+    sc = wl.room_scene()
+    sim = make_sim(p)
+    sid = sim.add_workload_scene(sc)
+    sim.set_swarm(HALF, RGB, LABEL)
+    n = 600
+    st = _cluster(wl, sc, n, 90 + wh[0], spread=2.5)
+    ids = torch.full((n,), sid, dtype=torch.int32, device="cuda")
+    d, c, h = _gpu_render(sim, ids, st)
+    pick = np.random.default_rng(wh[0] * 31 + wh[1]).choice(n, 24, replace=False)
+    osc = oracle_mod.Scene.from_workload(sc)
+    st64 = st.astype(np.float64)
+    sw = {"half": HALF, "rgb": RGB, "states": st64, "self": pick}
+    ref = osc.render(p, st64[pick], swarm=sw)
+    assert (ref["id"] <= -2).any()                     # some sampled pixels see another drone
+    clear = ~ref["tie"]
+    assert np.array_equal(h[pick][clear], ref["id"][clear])
+    assert np.array_equal(c[pick][clear], ref["rgb"][clear])
+    assert np.all(np.abs(d[pick][clear] - ref["depth"][clear]) <= DEPTH_TOL * ref["depth"][clear])
+    ties = np.flatnonzero(ref["tie"].ravel())
+    if ties.size:
+        ok = osc.validate(p, st64[pick], ties, h[pick].ravel()[ties], d[pick].ravel()[ties], swarm=sw)
+        assert ok.all(), f"{(~ok).sum()} of {ties.size} tie pixels not admissible"
