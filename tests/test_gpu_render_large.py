@@ -82,3 +82,40 @@ def test_multi_scene_launch_beyond_l2_prefetch(make_sim, oracle_mod, wl):
         ties += stats["ties"]
         pixels += stats["pixels"]
     assert ties < 0.01 * pixels, (ties, pixels)
+
+
+def test_batched_workload_full_size_sampled_parity(make_sim, oracle_mod, wl):
+    """The multi-scene workload at the size the benchmark times it: 64 scenes
+    of 10k-1M triangles (log-uniform sizes, seeds 100-163), 4,096 agents spread
+    over them by Zipf(1.1), one launch through the scene table (3.4 GB of
+    BVHs and triangles, far past the L2 prefetch limit).  Eight sampled agents
+    (in the largest scene, the smallest and six others) match the oracle, and
+    the images of every agent equal those of the configuration the autotuner
+    picks for this workload (8x8 tiles, two rays per lane, a 48-entry
+    shared-memory stack)."""
+    p = wl.params()
+    sizes = wl.Rng(99).log_uniform(10_000, 1_000_000, 64)
+    scenes = [wl.sized_scene(int(t), 100 + i) for i, t in enumerate(sizes)]
+    counts = wl.zipf_partition(4096, 64, 1.1, 7)
+    sim = make_sim(p)
+    sids = [sim.add_workload_scene(s) for s in scenes]
+    stack = sim.render_config()["stack_depth"]
+    assert all(0 < sim.scene_info(s)["depth"] <= stack for s in sids)
+    states = [wl.spawn_states(s, int(k), 1000 + i, 1100.0).astype(np.float32)
+              for i, (s, k) in enumerate(zip(scenes, counts))]
+    all_s = np.concatenate(states)
+    ids = torch.tensor(np.repeat(sids, counts), dtype=torch.int32, device="cuda")
+    d, c, h = _render(sim, ids, all_s)
+    off = np.concatenate([[0], np.cumsum(counts)])
+    rng = np.random.default_rng(64)
+    picks = {int(np.argmax(sizes)), int(np.argmin(sizes))}
+    while len(picks) < 8:
+        picks.add(int(rng.integers(64)))
+    for s in sorted(picks):
+        a = off[s] + int(rng.integers(counts[s]))
+        compare_images(oracle_mod.Scene.from_workload(scenes[s]), p, all_s[a:a + 1].astype(np.float64), d[a:a + 1],
+                       c[a:a + 1], h[a:a + 1], max_tie_frac=0.05)
+    sim.set_render_config({**sim.render_config(), "tile_w": 8, "tile_h": 8, "rays_per_lane": 2, "stack_in_smem": 1,
+                           "stack_depth": 48})
+    for x, y in zip((d, c, h), _render(sim, ids, all_s)):
+        assert np.array_equal(x, y)
