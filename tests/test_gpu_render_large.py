@@ -119,3 +119,31 @@ def test_batched_workload_full_size_sampled_parity(make_sim, oracle_mod, wl):
                            "stack_depth": 48})
     for x, y in zip((d, c, h), _render(sim, ids, all_s)):
         assert np.array_equal(x, y)
+
+
+def test_serving_scene_set_sampled_parity(make_sim, oracle_mod, wl):
+    """The serving workload's resident scene set at full size: 32 scenes of
+    50k-2M triangles (log-uniform sizes, seeds 500-531, about 2.2 GB resident),
+    8 agents in each, one launch through the scene table; one sampled agent in
+    each of eight scenes (the largest and the smallest among them) matches the
+    oracle."""
+    p = wl.params()
+    sizes = wl.Rng(5).log_uniform(50_000, 2_000_000, 32)
+    scenes = [wl.sized_scene(int(t), 500 + i) for i, t in enumerate(sizes)]
+    sim = make_sim(p)
+    sids = [sim.add_workload_scene(s) for s in scenes]
+    stack = sim.render_config()["stack_depth"]
+    assert all(0 < sim.scene_info(s)["depth"] <= stack for s in sids)
+    k = 8
+    states = [wl.spawn_states(s, k, 600 + i, 1100.0).astype(np.float32) for i, s in enumerate(scenes)]
+    all_s = np.concatenate(states)
+    ids = torch.tensor(np.repeat(sids, k), dtype=torch.int32, device="cuda")
+    d, c, h = _render(sim, ids, all_s)
+    rng = np.random.default_rng(32)
+    picks = {int(np.argmax(sizes)), int(np.argmin(sizes))}
+    while len(picks) < 8:
+        picks.add(int(rng.integers(32)))
+    for s in sorted(picks):
+        a = s * k + int(rng.integers(k))
+        compare_images(oracle_mod.Scene.from_workload(scenes[s]), p, all_s[a:a + 1].astype(np.float64), d[a:a + 1],
+                       c[a:a + 1], h[a:a + 1], max_tie_frac=0.05)
